@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the hybrid demagnetization field (Eq. FFT_v2) on GB300.
+
+One step = one demagnetization-field evaluation of the workload (forward row
+FFTs, fused column FFT + layer contraction + inverse column FFT, inverse row
+FFTs) through the C ABI on device-resident inputs.  A 256 MB buffer (twice the
+L2) is written between timed steps so that every step starts from a cold L2;
+steps are timed with CUDA events on the launching stream.
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
+independently seeded states on its own GPU (replicas, weak scaling) and the
+slowest rank's time sets the value.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "demag evals/s and Gcell-layers/s at ≤1e-5 rel L2 vs FP64 oracle; % HBM peak"
+WORKLOAD = "mram256"
+FLUSH_BYTES = 256 << 20
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--cpu-budget", type=float, default=20.0,
+                   help="seconds of oracle evaluation for the CPU baseline sample")
+    p.add_argument("--no-parity", action="store_true", help="skip the oracle field comparison")
+    return p.parse_args()
+
+
+def workload():
+    from paper_1910_07054_gb300 import inputs
+    c = inputs.CONFIGS[WORKLOAD]
+    th = [float(t) for t in inputs.thicknesses(WORKLOAD)]
+    desc = ("MRAM-like stack: %dx%d cells of %gx%g nm, %d layers of %s nm, batch %d; odd layers two "
+            "+-z half-plane domains, even layers seeded random unit vectors; Ms = %g A/m; float32 "
+            "FFTs and contraction, float64 tensor set-up"
+            % (c["nx"], c["ny"], c["dx"], c["dy"], len(th), th, c["batch"], inputs.MS_DEFAULT))
+    return c, th, desc
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the GPU works."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = sorted(v for v in sm if smax and v > 0.5 * smax) or sorted(sm)
+        med = loaded[len(loaded) // 2] if loaded else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = json.load(fh).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("apply.cu", "fft.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_07054_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    ent = rec.get("kernels", {}).get(kernel)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+def oracle_setup(c, th):
+    """Oracle spectra of the workload's layer kernels (float64, CPU)."""
+    from oracle import demag as odm
+    from oracle import newell as onw
+    Kq = onw.layer_kernels(c["nx"], c["ny"], c["dx"], c["dy"], th, mode=onw.READING_D, full=False)
+    return odm.padded_kernel_spectra(odm.expand_quadrant(Kq))
+
+
+def oracle_timed(Khat, m_np, Ms, budget_s, max_evals):
+    """Times whole oracle evaluations of the workload until budget_s is spent."""
+    from oracle import demag as odm
+    times, H = [], None
+    t_start = time.perf_counter()
+    while len(times) < max_evals:
+        t0 = time.perf_counter()
+        H = odm.hybrid(None, m_np, Ms, Khat=Khat)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return times, H
+
+
+def run_reference(args):
+    """The oracle (float64 numpy + C) on the host cores, whole evaluations of the
+    same workload; at most --steps evaluations after --warmup, bounded in time."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_1910_07054_gb300 import inputs
+    c, th, desc = workload()
+    m = inputs.mram_magnetization(c["nx"], c["ny"], len(th), seed=0, batch=c["batch"])
+    t0 = time.perf_counter()
+    Khat = oracle_setup(c, th)
+    setup_s = time.perf_counter() - t0
+    warm = min(args.warmup, 1)
+    oracle_timed(Khat, m, inputs.MS_DEFAULT, 0.0, warm)
+    times, _ = oracle_timed(Khat, m, inputs.MS_DEFAULT, args.cpu_budget * 3, args.steps)
+    per = float(np.mean(times))
+    value = c["batch"] / per
+    sample = ("%d whole evaluations of the workload (of %d steps requested) after %d warm-up, oracle "
+              "float64 hybrid (numpy FFT, single thread); tensor set-up %.1f s not timed"
+              % (len(times), args.steps, warm, setup_s))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 0,
+            "steps": len(times), "warmup": warm, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "parallelism": "host cores"},
+            "gcell_layers_per_s": c["nx"] * c["ny"] * len(th) * value / 1e9,
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import inputs
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    c, th, desc = workload()
+    nx, ny, L, B = c["nx"], c["ny"], len(th), c["batch"]
+    Ms = inputs.MS_DEFAULT
+    m_np = inputs.mram_magnetization(nx, ny, L, seed=rank, batch=B)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_FP32, max_batch=B)
+    plan_s = time.perf_counter() - t0
+    info = plan.info
+    m = torch.tensor(m_np, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(m)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for k in range(args.warmup):
+        flush.fill_(float(k))
+        dm.demag_apply(plan.handle, m, Ms, H, stream, info)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        dm.demag_apply(plan.handle, m, Ms, H, stream, info)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    T = float(step_ms.mean())
+    if dist:
+        t = torch.tensor([T], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+    value = world * B / (T * 1e-3)
+
+    # per-kernel device times (same kernels, events between them, cold L2 each step)
+    nk = min(args.steps, 200)
+    stage = np.zeros(3)
+    for k in range(nk):
+        flush.fill_(float(k))
+        stage += np.array(dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info))
+    stage /= nk
+
+    # end to end through the host entry point (pinned buffers, copies included)
+    mh = torch.tensor(m_np, dtype=torch.float32).pin_memory()
+    Hh = torch.empty_like(mh).pin_memory()
+    ne = min(args.steps, 200)
+    dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    e0 = time.perf_counter()
+    for _ in range(ne):
+        dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    e2e_s = (time.perf_counter() - e0) / ne
+    clk = clocks.stop()
+
+    # algorithmic bytes per launch (float32, B states)
+    Kx, Qy, npairs = info["Px"] // 2 + 1, info["Py"] // 2 + 1, info["npairs"]
+    field = B * L * 3 * ny * nx * 4
+    spec = B * L * 3 * Kx * ny * 8
+    tensor = Kx * npairs * 6 * Qy * 4
+    stage_bytes = [field + spec, 2 * spec + tensor, spec + field]
+    names = ["k_rows_forward", "k_columns_fused", "k_rows_inverse"]
+    dom = int(np.argmax(stage))
+    peak, peak_kind = measured_hbm_peak()
+    achieved = stage_bytes[dom] / (stage[dom] * 1e-3) / 1e9
+    traffic = recorded_traffic(names[dom])
+
+    line = None
+    if rank == 0:
+        H_host = H.double().cpu().numpy()
+        rel = None
+        cpu = None
+        if not args.no_parity or world == 1:
+            Khat = oracle_setup(c, th)
+            if world == 1:
+                times, H_ref = oracle_timed(Khat, m_np, Ms, args.cpu_budget, 1000)
+                cpu = {"value": B / float(np.mean(times)), "unit": "evals/s", "cores": 1, "kind": "oracle",
+                       "sample": "%d whole evaluations of the workload, oracle float64 hybrid (numpy "
+                                 "FFT, single thread), tensor set-up not timed" % len(times)}
+            else:
+                from oracle import demag as odm
+                H_ref = odm.hybrid(None, m_np, Ms, Khat=Khat)
+            if not args.no_parity:
+                rel = float(np.linalg.norm(H_host - H_ref) / np.linalg.norm(H_ref))
+        min_bytes = 2 * field + tensor
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": T, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "nx": nx, "ny": ny, "layers": L, "batch_per_gpu": B,
+                       "padded_fft": [info["Px"], info["Py"]],
+                       "l2": "256 MB buffer written between timed steps (cold L2 per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gcell_layers_per_s": nx * ny * L * value / 1e9,
+            "rel_l2_vs_oracle": rel,
+            "hbm_frac_min_bytes": (min_bytes / (T * 1e-3) / 1e9) / peak,
+            "kernels_ms": dict(zip(names, [float(v) for v in stage])),
+            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes": stage_bytes[dom]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * B / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": field,
+                    "d2h_bytes_per_step": field},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "plan_create_s": plan_s,
+            "wall_s_timed_loop": wall,
+        }
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

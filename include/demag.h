@@ -1,0 +1,186 @@
+/*
+ * demag.h - C ABI of the GB300 (sm_103a) hybrid demagnetization-field library.
+ *
+ * The library computes the demagnetization field of a stack of magnetic layers
+ * that share a regular nx x ny in-plane grid of cells dx x dy but have
+ * individual thicknesses t[0..L-1] (the "non-equidistant" case of Sec. 3 of
+ * Heistracher et al., "Hybrid FFT algorithm for fast demagnetization field
+ * calculations on non-equidistant magnetic layers"):
+ *
+ *     H_i = -Ms * sum_j N(i <- j) m_j                       (Sec. 3, Eq. Hi_discrete)
+ *
+ * evaluated as in Eq. FFT_v2: zero-padded 2D FFTs of every layer's
+ * magnetization in x and y, an explicit sum over the source layers j at every
+ * in-plane frequency with 3x3 generalized-Newell tensor blocks, and an inverse
+ * 2D FFT cropped to the grid.  N(i <- j) is the generalized Newell tensor of
+ * Sec. 2 (Eqs. Nxx and Nxy, App. A and B) between a target cell of thickness
+ * t[i] and a source cell of thickness t[j], normalised by the target volume.
+ *
+ * Conventions shared by every entry point:
+ *   - Layers are stacked contiguously from z = 0 upward; layer 0 is the bottom.
+ *     A non-magnetic layer (spacer) is a layer whose m is zero.
+ *   - Arrays of vectors are [B][L][3][ny][nx], x fastest, component order
+ *     (x, y, z), dense, in the plan's real type (double for DEMAG_PREC_FP64,
+ *     float otherwise).  m is dimensionless (unit vectors or zero), Ms and H
+ *     in A/m.  Lengths (dx, dy, thickness) in any common unit (the tensor is
+ *     dimensionless); nm by convention.
+ *   - Device pointers are CUDA device memory of the device that was current
+ *     when the plan was created.  "stream" is a cudaStream_t passed as void*
+ *     (NULL = the legacy default stream).  Work is ordered on that stream; no
+ *     entry point synchronises unless it says so.
+ *   - The caller owns every buffer it passes; the plan owns its own device
+ *     memory (tensor, workspaces) and frees it in demag_destroy.
+ *   - Every entry point returns a demag_status and never aborts.  On failure
+ *     demag_last_error() returns a message for the calling host thread.
+ *   - A plan may be used by one host thread at a time; applies on different
+ *     streams with the same plan share its workspace and must not overlap.
+ */
+#ifndef DEMAG_H
+#define DEMAG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DEMAG_OK = 0,
+    DEMAG_EINVAL = 1,        /* an argument is invalid (size, pointer, value)  */
+    DEMAG_ENOMEM = 2,        /* a device or host allocation failed            */
+    DEMAG_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed   */
+    DEMAG_EUNSUPPORTED = 4   /* valid but outside this build's limits         */
+} demag_status;
+
+typedef enum {
+    DEMAG_PREC_FP64 = 0,     /* FFTs and layer contraction in double          */
+    DEMAG_PREC_FP32 = 1      /* FFTs and layer contraction in float           */
+} demag_precision;
+
+typedef struct demag_plan *demag_plan_t;
+
+/* Human-readable name of a status code (static string). */
+const char *demag_status_string(demag_status status);
+
+/* Detail of the last failure on the calling host thread ("" if none). */
+const char *demag_last_error(void);
+
+/*
+ * demag_plan_create - build the Fourier-space layer tensor of a layer stack.
+ *
+ * Sec. 2 (generalized Newell tensor) and Sec. 3 (Eq. FFT_v2).  For every pair
+ * of layers (target i, source j) and every in-plane offset (p dx, q dy),
+ * |p| < nx, |q| < ny, the six components of N(i <- j) are evaluated in double
+ * precision on the GPU, zero-padded onto the circulant grid (the next powers
+ * of two >= 2nx and >= 2ny), transformed by a double-precision 2D FFT and
+ * stored in the plan's real type.  Far cells, where the closed form loses its
+ * digits to cancellation, use a quadrature of the same volume integral.
+ *
+ *   plan       out: the new plan (unchanged on failure)
+ *   nx, ny     in-plane cells, 1 <= nx, ny <= 2048
+ *   dx, dy     in-plane cell edges, > 0 and finite
+ *   thickness  HOST array of L layer thicknesses, each > 0 and finite
+ *   L          number of layers, 1 <= L <= 256
+ *   precision  a demag_precision value
+ *   max_batch  largest batch B later passed to demag_apply, >= 1
+ *   stream     stream for the set-up work; the call synchronises this stream
+ *              before it returns
+ *
+ * Errors: DEMAG_EINVAL (bad argument), DEMAG_EUNSUPPORTED (limits, or a layer
+ * count the precision's contraction kernels do not cover), DEMAG_ENOMEM,
+ * DEMAG_ECUDA.
+ */
+demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, double dy,
+                               const double *thickness, int L, int precision, int max_batch,
+                               void *stream);
+
+/*
+ * demag_apply - demagnetization field of B magnetization states.
+ *
+ * Eq. FFT_v2 read right to left: forward real-to-complex FFT along x of every
+ * row, FFT along y, H_k(i) = sum_j N_k(i <- j) m_k(j) at every frequency k,
+ * inverse FFT along y, inverse complex-to-real FFT along x cropped to the
+ * grid, scaled by -Ms (Eq. Hi_discrete).
+ *
+ *   m      DEVICE, [B][L][3][ny][nx] of the plan's real type, read only
+ *   Ms     saturation magnetization (A/m), finite
+ *   H      DEVICE, same shape and type as m, written (must not alias m)
+ *   B      1 <= B <= max_batch of the plan
+ *   stream stream to order the work on (asynchronous)
+ */
+demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, int B,
+                         void *stream);
+
+/*
+ * demag_apply_host - demag_apply on HOST buffers (end-to-end call).
+ *
+ * Copies m from host to the plan's device staging buffer, runs demag_apply,
+ * copies H back to the host and synchronises the stream.  Host buffers should
+ * be pinned (cudaHostAlloc) for full copy bandwidth; pageable memory works.
+ *
+ *   m, H   HOST, [B][L][3][ny][nx] of the plan's real type
+ *   other arguments as in demag_apply
+ */
+demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, void *H_host,
+                              int B, void *stream);
+
+/*
+ * demag_apply_timed - demag_apply with per-kernel device timing.
+ *
+ * Runs exactly the kernels of demag_apply on the device buffers m and H, with
+ * CUDA events recorded on `stream` before the first kernel and after each
+ * kernel, then synchronises the stream and writes the elapsed times:
+ *   stage_ms (HOST, nstage values, nstage >= 3):
+ *     [0] forward row transforms, [1] column transforms + layer contraction,
+ *     [2] inverse row transforms (milliseconds, CUDA event resolution).
+ * Other arguments as in demag_apply.
+ */
+demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void *H, int B,
+                               void *stream, float *stage_ms, int nstage);
+
+/*
+ * demag_plan_info - sizes of a plan.
+ *
+ * out (HOST, 8 values): {nx, ny, L, Px, Py, precision, max_batch,
+ *                        number of stored layer pairs}
+ * Px, Py are the padded FFT sizes; the stored tensor holds the layer pairs
+ * i <= j (the rest follow from reciprocity, t_i N(i<-j)(d) = t_j N(j<-i)(-d)).
+ */
+demag_status demag_plan_info(demag_plan_t plan, long long *out);
+
+/*
+ * demag_plan_tensor - copy of the stored Fourier-space tensor.
+ *
+ * out DEVICE, (Px/2+1) * npairs * 6 * (Py/2+1) values of the plan's real type,
+ * layout [kx][pair][component][ky] with pair (i <= j) numbered row by row
+ * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components
+ * {Re N_xx, Re N_yy, Re N_zz, Re N_xy, Im N_xz, Im N_yz} of the 2D DFT of
+ * N(i <- j) on the padded grid, divided by Px*Py.  bytes is the size of out.
+ * Asynchronous on stream.
+ */
+demag_status demag_plan_tensor(demag_plan_t plan, void *out, size_t bytes, void *stream);
+
+/*
+ * demag_tensor_points - the generalized Newell tensor at arbitrary geometries.
+ *
+ * Sec. 2, Eqs. Nxx and Nxy with App. A/B (closed form, double precision) for
+ * near pairs of cuboids, and a composite Gauss-Legendre quadrature of the
+ * defining volume integral (Eq. demag_tensor) for pairs further apart than the
+ * larger in-plane edge.  This is the evaluation the plan builder uses.
+ *
+ *   n      number of points, >= 0
+ *   geom   DEVICE double [n][9]: X, Y, Z (target corner minus source corner),
+ *          target edges tx, ty, tz, source edges sx, sy, sz (all edges > 0)
+ *   out    DEVICE double [n][6]: N_xx, N_yy, N_zz, N_xy, N_xz, N_yz of
+ *          N(target <- source), normalised by the target volume
+ */
+demag_status demag_tensor_points(int n, const double *geom, double *out, void *stream);
+
+/* demag_destroy - free a plan (NULL is accepted).  Synchronises the device. */
+demag_status demag_destroy(demag_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEMAG_H */

@@ -32,12 +32,12 @@ def expand_quadrant(Kq):
     L1, L2, C, ny, nx = Kq.shape
     sx = np.array([1, 1, 1, -1, -1, 1], dtype=np.float64)  # sign under X -> -X
     sy = np.array([1, 1, 1, -1, 1, -1], dtype=np.float64)  # sign under Y -> -Y
-    K = np.zeros((L1, L2, C, 2 * ny - 1, 2 * nx - 1))
-    for q in range(-(ny - 1), ny):
-        for p in range(-(nx - 1), nx):
-            sgn = (sx if p < 0 else 1.0) * (sy if q < 0 else 1.0)
-            K[:, :, :, q + ny - 1, p + nx - 1] = Kq[:, :, :, abs(q), abs(p)] * sgn
-    return K
+    qs = np.arange(-(ny - 1), ny)
+    ps = np.arange(-(nx - 1), nx)
+    K = Kq[:, :, :, np.abs(qs)[:, None], np.abs(ps)[None, :]]
+    sgn_x = np.where(ps[None, :] < 0, sx[:, None], 1.0)  # [6, 2nx-1]
+    sgn_y = np.where(qs[None, :] < 0, sy[:, None], 1.0)  # [6, 2ny-1]
+    return K * (sgn_y[:, :, None] * sgn_x[:, None, :])
 
 
 def direct_sum(K, m, Ms):

@@ -1,0 +1,215 @@
+"""ctypes binding of libdemag (``include/demag.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks tensor shapes, dtypes and devices, passes
+raw pointers and the current CUDA stream, and raises ``DemagError`` on a
+non-zero status.  The library is built in-tree by ``build.py`` and loaded from
+``_build/libdemag.so``; if it cannot be built or loaded, every call raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+DEMAG_OK, DEMAG_EINVAL, DEMAG_ENOMEM, DEMAG_ECUDA, DEMAG_EUNSUPPORTED = range(5)
+PREC_FP64, PREC_FP32 = 0, 1
+
+_lib = None
+
+
+class DemagError(RuntimeError):
+    def __init__(self, status, where, detail):
+        self.status = status
+        super().__init__("%s failed: %s (%s)" % (where, _status_name(status), detail))
+
+
+def _status_name(s):
+    return {0: "DEMAG_OK", 1: "DEMAG_EINVAL", 2: "DEMAG_ENOMEM", 3: "DEMAG_ECUDA",
+            4: "DEMAG_EUNSUPPORTED"}.get(s, "status %d" % s)
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) libdemag.so; raises if that is impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libdemag.so is missing at %s" % path)
+    L = ctypes.CDLL(path)
+    vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    L.demag_status_string.argtypes = [i]
+    L.demag_status_string.restype = ctypes.c_char_p
+    L.demag_last_error.argtypes = []
+    L.demag_last_error.restype = ctypes.c_char_p
+    L.demag_plan_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, dp, i, i, i, vp]
+    L.demag_plan_create.restype = i
+    L.demag_apply.argtypes = [vp, vp, d, vp, i, vp]
+    L.demag_apply.restype = i
+    L.demag_apply_timed.argtypes = [vp, vp, d, vp, i, vp, ctypes.POINTER(ctypes.c_float), i]
+    L.demag_apply_timed.restype = i
+    L.demag_apply_host.argtypes = [vp, vp, d, vp, i, vp]
+    L.demag_apply_host.restype = i
+    L.demag_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.demag_plan_info.restype = i
+    L.demag_plan_tensor.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.demag_plan_tensor.restype = i
+    L.demag_tensor_points.argtypes = [i, vp, vp, vp]
+    L.demag_tensor_points.restype = i
+    L.demag_destroy.argtypes = [vp]
+    L.demag_destroy.restype = i
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != DEMAG_OK:
+        detail = lib().demag_last_error().decode(errors="replace")
+        raise DemagError(status, where, detail)
+
+
+def _stream(stream):
+    """cudaStream_t of a torch stream (or the current stream) as void*."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def demag_status_string(status):
+    return lib().demag_status_string(int(status)).decode()
+
+
+def demag_last_error():
+    return lib().demag_last_error().decode(errors="replace")
+
+
+def demag_plan_create(nx, ny, dx, dy, thickness, precision=PREC_FP32, max_batch=1, stream=None):
+    """Returns an opaque plan handle (int).  thickness: sequence of L floats."""
+    th = (ctypes.c_double * len(thickness))(*[float(t) for t in thickness])
+    handle = ctypes.c_void_p()
+    _check(lib().demag_plan_create(ctypes.byref(handle), int(nx), int(ny), float(dx), float(dy), th,
+                                   len(thickness), int(precision), int(max_batch), _stream(stream)),
+           "demag_plan_create")
+    return handle.value
+
+
+def demag_plan_info(plan):
+    out = (ctypes.c_longlong * 8)()
+    _check(lib().demag_plan_info(ctypes.c_void_p(plan), out), "demag_plan_info")
+    keys = ("nx", "ny", "L", "Px", "Py", "precision", "max_batch", "npairs")
+    return dict(zip(keys, [int(v) for v in out]))
+
+
+def _field_check(t, info, name, device=True):
+    import torch
+    want = torch.float64 if info["precision"] == PREC_FP64 else torch.float32
+    if t.dtype != want:
+        raise TypeError("%s must be %s for this plan, got %s" % (name, want, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if device and not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not device and t.is_cuda:
+        raise ValueError("%s must be a host tensor" % name)
+    shape = tuple(t.shape)
+    tail = (info["L"], 3, info["ny"], info["nx"])
+    if shape[-4:] != tail or len(shape) not in (4, 5):
+        raise ValueError("%s must have shape [B, %d, 3, %d, %d] or [%d, 3, %d, %d], got %s"
+                         % (name, tail[0], tail[2], tail[3], tail[0], tail[2], tail[3], shape))
+    return 1 if len(shape) == 4 else shape[0]
+
+
+def demag_apply(plan, m, Ms, H, stream=None, info=None):
+    """H <- demag field of m (device tensors of the plan's dtype, [B, L, 3, ny, nx])."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(m, info, "m")
+    if _field_check(H, info, "H") != B or H.shape != m.shape:
+        raise ValueError("H must have the shape of m")
+    _check(lib().demag_apply(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
+                             ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)), "demag_apply")
+    return H
+
+
+def demag_apply_timed(plan, m, Ms, H, stream=None, info=None):
+    """demag_apply with per-kernel event times; returns [rows fwd, columns, rows inv] in ms."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(m, info, "m")
+    if _field_check(H, info, "H") != B or H.shape != m.shape:
+        raise ValueError("H must have the shape of m")
+    ms = (ctypes.c_float * 3)()
+    _check(lib().demag_apply_timed(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
+                                   ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream), ms, 3),
+           "demag_apply_timed")
+    return [float(v) for v in ms]
+
+
+def demag_apply_host(plan, m, Ms, H, stream=None, info=None):
+    """demag_apply on host tensors (pinned for full copy speed); synchronises."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(m, info, "m", device=False)
+    if _field_check(H, info, "H", device=False) != B or H.shape != m.shape:
+        raise ValueError("H must have the shape of m")
+    _check(lib().demag_apply_host(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
+                                  ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)),
+           "demag_apply_host")
+    return H
+
+
+def demag_plan_tensor(plan, out, stream=None):
+    _check(lib().demag_plan_tensor(ctypes.c_void_p(plan), ctypes.c_void_p(out.data_ptr()),
+                                   out.numel() * out.element_size(), _stream(stream)),
+           "demag_plan_tensor")
+    return out
+
+
+def demag_tensor_points(geom, out, stream=None):
+    """geom: CUDA float64 [n, 9]; out: CUDA float64 [n, 6]."""
+    import torch
+    if geom.dtype != torch.float64 or out.dtype != torch.float64 or not geom.is_cuda or not out.is_cuda:
+        raise TypeError("geom and out must be CUDA float64 tensors")
+    if geom.shape[-1] != 9 or out.shape[-1] != 6 or geom.shape[0] != out.shape[0]:
+        raise ValueError("geom must be [n, 9] and out [n, 6]")
+    _check(lib().demag_tensor_points(int(geom.shape[0]), ctypes.c_void_p(geom.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "demag_tensor_points")
+    return out
+
+
+def demag_destroy(plan):
+    if plan:
+        _check(lib().demag_destroy(ctypes.c_void_p(plan)), "demag_destroy")
+
+
+class Plan:
+    """Owning wrapper of a demag plan handle."""
+
+    def __init__(self, nx, ny, dx, dy, thickness, precision=PREC_FP32, max_batch=1, stream=None):
+        self.handle = demag_plan_create(nx, ny, dx, dy, thickness, precision, max_batch, stream)
+        self.info = demag_plan_info(self.handle)
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.info["precision"] == PREC_FP64 else torch.float32
+
+    def apply(self, m, Ms, H=None, stream=None):
+        import torch
+        if H is None:
+            H = torch.empty_like(m)
+        return demag_apply(self.handle, m, Ms, H, stream, self.info)
+
+    def close(self):
+        if self.handle:
+            demag_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,390 @@
+// C ABI of libdemag: plan lifecycle, argument checks and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace demag {
+
+static thread_local std::string g_last_error;
+
+demag_status fail(demag_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+demag_status cuda_fail(cudaError_t err, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+    g_last_error = m;
+    return err == cudaErrorMemoryAllocation ? DEMAG_ENOMEM : DEMAG_ECUDA;
+}
+
+static int ilog2_ceil(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// exp(-2 pi i k / N) for k < N/2, N = 2^log2n
+template <typename C>
+static std::vector<C> twiddles(int log2n) {
+    const int N = 1 << log2n;
+    std::vector<C> tw(N / 2 > 0 ? N / 2 : 1);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < N / 2; ++k) {
+        const double ang = 2.0 * pi * (double)k / (double)N;
+        tw[k].x = std::cos(ang);
+        tw[k].y = -std::sin(ang);
+    }
+    if (N / 2 == 0) tw[0] = C{1, 0};
+    return tw;
+}
+
+static void free_plan(demag_plan *p) {
+    if (!p) return;
+    cudaFree(p->d_tensor);
+    cudaFree(p->d_ratio);
+    cudaFree(p->d_twx);
+    cudaFree(p->d_twy);
+    cudaFree(p->d_spec);
+    cudaFree(p->d_stage_m);
+    cudaFree(p->d_stage_H);
+    delete p;
+}
+
+// Device allocation that records the failure.
+static demag_status dalloc(void **ptr, size_t bytes, const char *what) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? DEMAG_ENOMEM : DEMAG_ECUDA,
+                    std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " bytes): " +
+                        cudaGetErrorString(e));
+    }
+    return DEMAG_OK;
+}
+
+#define DEMAG_TRY(expr)                       \
+    do {                                      \
+        demag_status s_ = (expr);             \
+        if (s_ != DEMAG_OK) return s_;        \
+    } while (0)
+
+static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
+    const int L = p->L;
+    std::vector<int> pi, pj;
+    for (int i = 0; i < L; ++i)
+        for (int j = i; j < L; ++j) {
+            pi.push_back(i);
+            pj.push_back(j);
+        }
+    std::vector<double> z(L + 1, 0.0);
+    for (int l = 0; l < L; ++l) z[l + 1] = z[l] + p->thickness[l];
+
+    const int Px = 1 << p->log2Px, Py = 1 << p->log2Py;
+    const size_t plane_bytes = (size_t)3 * Px * Py * sizeof(double2);
+    // pairs per chunk: bounded workspace (~4 GB)
+    int chunk = 1;
+    {
+        size_t budget = (size_t)4 << 30;
+        size_t c = budget / plane_bytes;
+        if (c < 1) c = 1;
+        if (c > (size_t)p->npairs) c = p->npairs;
+        chunk = (int)c;
+    }
+    int *d_pi = nullptr, *d_pj = nullptr;
+    double *d_z = nullptr, *d_th = nullptr;
+    double2 *planes = nullptr, *twx = nullptr, *twy = nullptr;
+    demag_status rc = DEMAG_OK;
+    auto cleanup = [&]() {
+        cudaFree(d_pi);
+        cudaFree(d_pj);
+        cudaFree(d_z);
+        cudaFree(d_th);
+        cudaFree(planes);
+        cudaFree(twx);
+        cudaFree(twy);
+    };
+    do {
+        if ((rc = dalloc((void **)&d_pi, pi.size() * sizeof(int), "pair list")) != DEMAG_OK) break;
+        if ((rc = dalloc((void **)&d_pj, pj.size() * sizeof(int), "pair list")) != DEMAG_OK) break;
+        if ((rc = dalloc((void **)&d_z, z.size() * sizeof(double), "interfaces")) != DEMAG_OK) break;
+        if ((rc = dalloc((void **)&d_th, L * sizeof(double), "thicknesses")) != DEMAG_OK) break;
+        if ((rc = dalloc((void **)&planes, plane_bytes * chunk, "tensor planes")) != DEMAG_OK) break;
+        auto htwx = twiddles<double2>(p->log2Px), htwy = twiddles<double2>(p->log2Py);
+        if ((rc = dalloc((void **)&twx, htwx.size() * sizeof(double2), "twiddles")) != DEMAG_OK) break;
+        if ((rc = dalloc((void **)&twy, htwy.size() * sizeof(double2), "twiddles")) != DEMAG_OK) break;
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(d_pi, pi.data(), pi.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d_pj, pj.data(), pj.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d_z, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d_th, p->thickness.data(), L * sizeof(double), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(twx, htwx.data(), htwx.size() * sizeof(double2), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(twy, htwy.data(), htwy.size() * sizeof(double2), cudaMemcpyHostToDevice, st))) {
+            rc = cuda_fail(e, "cudaMemcpyAsync(tensor set-up)");
+            break;
+        }
+        for (int p0 = 0; p0 < p->npairs && rc == DEMAG_OK; p0 += chunk) {
+            const int np = std::min(chunk, p->npairs - p0);
+            if ((e = cudaMemsetAsync(planes, 0, plane_bytes * np, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "cudaMemsetAsync(tensor planes)");
+                break;
+            }
+            if ((e = launch_kernel_planes(planes, p0, np, d_pi, d_pj, p->nx, p->ny, p->dx, p->dy,
+                                          p->log2Px, p->log2Py, d_z, d_th, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "tensor evaluation kernel");
+                break;
+            }
+            if ((e = launch_fft2_planes(planes, 3 * np, p->log2Px, p->log2Py, twx, p->log2Px, twy,
+                                        p->log2Py, st)) != cudaSuccess) {
+                rc = cuda_fail(e, "tensor FFT kernels");
+                break;
+            }
+            if ((e = launch_extract_tensor(planes, p0, np, p->npairs, p->log2Px, p->log2Py,
+                                           p->d_tensor, p->precision == DEMAG_PREC_FP64, st)) !=
+                cudaSuccess) {
+                rc = cuda_fail(e, "tensor extraction kernel");
+                break;
+            }
+        }
+        if (rc != DEMAG_OK) break;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "tensor build");
+    } while (0);
+    cleanup();
+    return rc;
+}
+
+}  // namespace demag
+
+using namespace demag;
+
+extern "C" {
+
+const char *demag_status_string(demag_status s) {
+    switch (s) {
+        case DEMAG_OK: return "DEMAG_OK";
+        case DEMAG_EINVAL: return "DEMAG_EINVAL";
+        case DEMAG_ENOMEM: return "DEMAG_ENOMEM";
+        case DEMAG_ECUDA: return "DEMAG_ECUDA";
+        case DEMAG_EUNSUPPORTED: return "DEMAG_EUNSUPPORTED";
+    }
+    return "DEMAG_UNKNOWN";
+}
+
+const char *demag_last_error(void) { return g_last_error.c_str(); }
+
+demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, double dy,
+                               const double *thickness, int L, int precision, int max_batch,
+                               void *stream) {
+    g_last_error.clear();
+    if (!plan) return fail(DEMAG_EINVAL, "plan pointer is NULL");
+    if (!thickness) return fail(DEMAG_EINVAL, "thickness pointer is NULL");
+    if (nx < 1 || ny < 1) return fail(DEMAG_EINVAL, "nx and ny must be >= 1");
+    if (nx > 2048 || ny > 2048) return fail(DEMAG_EUNSUPPORTED, "nx and ny must be <= 2048");
+    if (L < 1) return fail(DEMAG_EINVAL, "L must be >= 1");
+    if (L > 256) return fail(DEMAG_EUNSUPPORTED, "L must be <= 256");
+    if (!(std::isfinite(dx) && dx > 0 && std::isfinite(dy) && dy > 0))
+        return fail(DEMAG_EINVAL, "dx and dy must be finite and > 0");
+    for (int l = 0; l < L; ++l)
+        if (!(std::isfinite(thickness[l]) && thickness[l] > 0))
+            return fail(DEMAG_EINVAL, "thickness[" + std::to_string(l) + "] must be finite and > 0");
+    if (precision != DEMAG_PREC_FP64 && precision != DEMAG_PREC_FP32)
+        return fail(DEMAG_EINVAL, "unknown precision");
+    if (max_batch < 1) return fail(DEMAG_EINVAL, "max_batch must be >= 1");
+    if ((long long)max_batch * L * 3 > 65535)
+        return fail(DEMAG_EUNSUPPORTED, "max_batch * L * 3 must be <= 65535");
+
+    demag_plan *p = new (std::nothrow) demag_plan();
+    if (!p) return fail(DEMAG_ENOMEM, "host allocation of the plan");
+    p->nx = nx;
+    p->ny = ny;
+    p->L = L;
+    p->dx = dx;
+    p->dy = dy;
+    p->precision = precision;
+    p->max_batch = max_batch;
+    p->thickness.assign(thickness, thickness + L);
+    p->log2Px = ilog2_ceil(2 * nx);
+    p->log2Py = ilog2_ceil(2 * ny);
+    if (p->log2Px < 2) p->log2Px = 2;
+    if (p->log2Py < 2) p->log2Py = 2;
+    p->Kx = (1 << p->log2Px) / 2 + 1;
+    p->Qy = (1 << p->log2Py) / 2 + 1;
+    p->npairs = L * (L + 1) / 2;
+    const bool fp64 = precision == DEMAG_PREC_FP64;
+    if (L > fused_max_layers(fp64, p->log2Py)) {
+        delete p;
+        return fail(DEMAG_EUNSUPPORTED, "layer count above the fused contraction limit for this grid");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    demag_status rc = upload_gauss_legendre();
+    const size_t real = fp64 ? sizeof(double) : sizeof(float);
+    const size_t cpx = 2 * real;
+    p->tensor_bytes = (size_t)p->Kx * p->npairs * 6 * p->Qy * real;
+    p->field_bytes_per_state = (size_t)L * 3 * ny * nx * real;
+    if (rc == DEMAG_OK) rc = dalloc(&p->d_tensor, p->tensor_bytes, "tensor");
+    if (rc == DEMAG_OK) rc = dalloc(&p->d_ratio, (size_t)L * L * real, "ratios");
+    if (rc == DEMAG_OK) rc = dalloc(&p->d_twx, (size_t)(1 << p->log2Px) / 2 * cpx, "twiddles");
+    if (rc == DEMAG_OK) rc = dalloc(&p->d_twy, (size_t)(1 << p->log2Py) / 2 * cpx, "twiddles");
+    if (rc == DEMAG_OK)
+        rc = dalloc(&p->d_spec, (size_t)max_batch * L * 3 * p->Kx * ny * cpx, "spectrum workspace");
+    if (rc == DEMAG_OK) {
+        // t_j / t_i for target i, source j (reciprocity of the stored pairs)
+        std::vector<double> r64((size_t)L * L);
+        for (int i = 0; i < L; ++i)
+            for (int j = 0; j < L; ++j) r64[(size_t)i * L + j] = thickness[j] / thickness[i];
+        auto tx64 = twiddles<double2>(p->log2Px), ty64 = twiddles<double2>(p->log2Py);
+        if (fp64) {
+            if ((e = cudaMemcpy(p->d_ratio, r64.data(), r64.size() * 8, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy(p->d_twx, tx64.data(), tx64.size() * 16, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy(p->d_twy, ty64.data(), ty64.size() * 16, cudaMemcpyHostToDevice)))
+                rc = cuda_fail(e, "cudaMemcpy(plan constants)");
+        } else {
+            std::vector<float> r32(r64.begin(), r64.end());
+            std::vector<float2> tx32(tx64.size()), ty32(ty64.size());
+            for (size_t k = 0; k < tx64.size(); ++k) tx32[k] = make_float2((float)tx64[k].x, (float)tx64[k].y);
+            for (size_t k = 0; k < ty64.size(); ++k) ty32[k] = make_float2((float)ty64[k].x, (float)ty64[k].y);
+            if ((e = cudaMemcpy(p->d_ratio, r32.data(), r32.size() * 4, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy(p->d_twx, tx32.data(), tx32.size() * 8, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy(p->d_twy, ty32.data(), ty32.size() * 8, cudaMemcpyHostToDevice)))
+                rc = cuda_fail(e, "cudaMemcpy(plan constants)");
+        }
+    }
+    if (rc == DEMAG_OK) rc = build_tensor(p, st);
+    if (rc != DEMAG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *plan = p;
+    return DEMAG_OK;
+}
+
+static demag_status check_apply(demag_plan_t plan, const void *m, double Ms, const void *H, int B) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    if (!m || !H) return fail(DEMAG_EINVAL, "m or H is NULL");
+    if (m == H) return fail(DEMAG_EINVAL, "H must not alias m");
+    if (B < 1 || B > plan->max_batch) return fail(DEMAG_EINVAL, "B must be in [1, max_batch]");
+    if (!std::isfinite(Ms)) return fail(DEMAG_EINVAL, "Ms must be finite");
+    return DEMAG_OK;
+}
+
+static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
+    ApplyArgs a;
+    a.nx = plan->nx;
+    a.ny = plan->ny;
+    a.L = plan->L;
+    a.B = B;
+    a.log2Px = plan->log2Px;
+    a.log2Py = plan->log2Py;
+    a.npairs = plan->npairs;
+    a.tensor = plan->d_tensor;
+    a.ratio = plan->d_ratio;
+    a.twx = plan->d_twx;
+    a.twy = plan->d_twy;
+    a.log2twx = plan->log2Px;
+    a.log2twy = plan->log2Py;
+    a.spec = plan->d_spec;
+    a.Ms = Ms;
+    return a;
+}
+
+demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, int B, void *stream) {
+    demag_status rc = check_apply(plan, m, Ms, H, B);
+    if (rc != DEMAG_OK) return rc;
+    cudaError_t e = launch_apply(apply_args(plan, Ms, B), m, H, plan->precision == DEMAG_PREC_FP64,
+                                 (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "demag_apply kernels");
+    return DEMAG_OK;
+}
+
+demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void *H, int B,
+                               void *stream, float *stage_ms, int nstage) {
+    demag_status rc = check_apply(plan, m, Ms, H, B);
+    if (rc != DEMAG_OK) return rc;
+    if (!stage_ms || nstage < kApplyStages) return fail(DEMAG_EINVAL, "stage_ms must hold 3 values");
+    cudaEvent_t ev[kApplyStages + 1] = {};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    int made = 0;
+    for (; made <= kApplyStages; ++made)
+        if ((e = cudaEventCreate(&ev[made])) != cudaSuccess) break;
+    if (e == cudaSuccess)
+        e = launch_apply(apply_args(plan, Ms, B), m, H, plan->precision == DEMAG_PREC_FP64, st, ev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int k = 0; e == cudaSuccess && k < kApplyStages; ++k)
+        e = cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]);
+    for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return cuda_fail(e, "demag_apply_timed");
+    return DEMAG_OK;
+}
+
+demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, void *H_host, int B,
+                              void *stream) {
+    demag_status rc = check_apply(plan, m_host, Ms, H_host, B);
+    if (rc != DEMAG_OK) return rc;
+    const size_t bytes = plan->field_bytes_per_state * (size_t)B;
+    if (!plan->d_stage_m) {
+        const size_t full = plan->field_bytes_per_state * (size_t)plan->max_batch;
+        DEMAG_TRY(dalloc(&plan->d_stage_m, full, "host staging"));
+        DEMAG_TRY(dalloc(&plan->d_stage_H, full, "host staging"));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    DEMAG_CUDA(cudaMemcpyAsync(plan->d_stage_m, m_host, bytes, cudaMemcpyHostToDevice, st));
+    cudaError_t e = launch_apply(apply_args(plan, Ms, B), plan->d_stage_m, plan->d_stage_H,
+                                 plan->precision == DEMAG_PREC_FP64, st);
+    if (e != cudaSuccess) return cuda_fail(e, "demag_apply_host kernels");
+    DEMAG_CUDA(cudaMemcpyAsync(H_host, plan->d_stage_H, bytes, cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(cudaStreamSynchronize(st));
+    return DEMAG_OK;
+}
+
+demag_status demag_plan_info(demag_plan_t plan, long long *out) {
+    if (!plan || !out) return fail(DEMAG_EINVAL, "plan or out is NULL");
+    out[0] = plan->nx;
+    out[1] = plan->ny;
+    out[2] = plan->L;
+    out[3] = 1LL << plan->log2Px;
+    out[4] = 1LL << plan->log2Py;
+    out[5] = plan->precision;
+    out[6] = plan->max_batch;
+    out[7] = plan->npairs;
+    return DEMAG_OK;
+}
+
+demag_status demag_plan_tensor(demag_plan_t plan, void *out, size_t bytes, void *stream) {
+    if (!plan || !out) return fail(DEMAG_EINVAL, "plan or out is NULL");
+    if (bytes != plan->tensor_bytes)
+        return fail(DEMAG_EINVAL, "out must hold exactly " + std::to_string(plan->tensor_bytes) + " bytes");
+    DEMAG_CUDA(cudaMemcpyAsync(out, plan->d_tensor, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return DEMAG_OK;
+}
+
+demag_status demag_tensor_points(int n, const double *geom, double *out, void *stream) {
+    if (n < 0) return fail(DEMAG_EINVAL, "n must be >= 0");
+    if (n > 0 && (!geom || !out)) return fail(DEMAG_EINVAL, "geom or out is NULL");
+    DEMAG_TRY(upload_gauss_legendre());
+    cudaError_t e = launch_tensor_points(n, geom, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor points kernel");
+    return DEMAG_OK;
+}
+
+demag_status demag_destroy(demag_plan_t plan) {
+    if (!plan) return DEMAG_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(plan);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize in demag_destroy");
+    return DEMAG_OK;
+}
+
+}  // extern "C"

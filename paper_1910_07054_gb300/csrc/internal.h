@@ -1,0 +1,90 @@
+// Internal interfaces between the translation units of libdemag.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+
+#include "../../include/demag.h"
+
+namespace demag {
+
+// Records a failure message for demag_last_error() and returns the status.
+demag_status fail(demag_status st, const std::string &msg);
+demag_status cuda_fail(cudaError_t err, const char *what);
+
+#define DEMAG_CUDA(call)                                                   \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return ::demag::cuda_fail(e_, #call);       \
+    } while (0)
+
+// Gauss-Legendre rules for n = 1..kGLMax, uploaded to constant memory once.
+constexpr int kGLMax = 8;
+demag_status upload_gauss_legendre();
+
+// Layer geometry on the device for the tensor builder.
+struct StackDev {
+    const double *z;   // [L+1] interface heights, z[0] = 0
+    const double *th;  // [L] thicknesses
+};
+
+// Evaluate n tensors at geom[n][9] (X,Y,Z,tx,ty,tz,sx,sy,sz) -> out[n][6].
+cudaError_t launch_tensor_points(int n, const double *geom, double *out, cudaStream_t st);
+
+// Fill the padded real-space kernels of pairs [p0, p0 + np) into three complex
+// double planes per pair ([np][3][Py][Px], x fastest), zeroed beforehand:
+// plane 0 = N_xx + i N_yy, plane 1 = N_zz + i N_xy, plane 2 = N_xz + i N_yz.
+cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pair_i,
+                                 const int *pair_j, int nx, int ny, double dx, double dy,
+                                 int log2Px, int log2Py, const double *z, const double *th,
+                                 cudaStream_t st);
+
+// In-place 2D FFT (forward, double) of nplanes planes [Py][Px].
+cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log2Py,
+                               const double2 *twx, int log2twx, const double2 *twy, int log2twy,
+                               cudaStream_t st);
+
+// Extract the stored quadrant of pairs [p0, p0+np) from transformed planes into
+// the plan tensor [Kx][npairs][6][Qy] (float or double), scaled by 1/(Px Py).
+cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs,
+                                  int log2Px, int log2Py, void *tensor, bool fp64,
+                                  cudaStream_t st);
+
+// ---- apply ---------------------------------------------------------------
+struct ApplyArgs {
+    int nx, ny, L, B;
+    int log2Px, log2Py;
+    int npairs;
+    const void *tensor;   // [Kx][npairs][6][Qy]
+    const void *ratio;    // [L][L]: t_j / t_i (plan real type)
+    const void *twx;      // twiddles for Px (complex of the plan type)
+    const void *twy;      // twiddles for Py
+    int log2twx, log2twy;
+    void *spec;           // [B][L][3][Kx][ny] complex workspace
+    double Ms;
+};
+
+// Largest layer count the fused column kernel handles for a precision.
+int fused_max_layers(bool fp64, int log2Py);
+// events (optional, may be null): [0] before the first kernel, [k] after kernel k.
+constexpr int kApplyStages = 3;
+cudaError_t launch_apply(const ApplyArgs &a, const void *m, void *H, bool fp64, cudaStream_t st,
+                         cudaEvent_t *events = nullptr);
+
+}  // namespace demag
+
+struct demag_plan {
+    int nx, ny, L, precision, max_batch;
+    double dx, dy;
+    int log2Px, log2Py, Kx, Qy, npairs;
+    std::vector<double> thickness;
+    void *d_tensor = nullptr;     // [Kx][npairs][6][Qy]
+    void *d_ratio = nullptr;      // [L][L]
+    void *d_twx = nullptr, *d_twy = nullptr;
+    void *d_spec = nullptr;       // [max_batch][L][3][Kx][ny] complex
+    void *d_stage_m = nullptr;    // staging for demag_apply_host
+    void *d_stage_H = nullptr;
+    size_t tensor_bytes = 0, field_bytes_per_state = 0;
+    int device = 0;
+};

@@ -1,0 +1,207 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Tolerances: float64 plans within 1e-11 relative L2 of the oracle field, float32
+plans within 1e-5 relative L2 (the accuracy target of this library); the
+tensor evaluation within 5e-13 of the largest component of the exact
+_Float128 tensor.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1910_07054_gb300 as dm
+from oracle import demag as odm
+from oracle import newell as onw
+from paper_1910_07054_gb300 import inputs
+from _cases import quad_kernels, reading_kernels, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def _gpu_field(nx, ny, dx, dy, th, m, Ms, prec, max_batch=None):
+    dtype = torch.float64 if prec == dm.PREC_FP64 else torch.float32
+    mt = torch.as_tensor(m, dtype=dtype, device="cuda").contiguous()
+    B = mt.shape[0] if mt.dim() == 5 else 1
+    plan = dm.Plan(nx, ny, dx, dy, th, precision=prec, max_batch=max_batch or B)
+    H = plan.apply(mt, Ms)
+    torch.cuda.synchronize()
+    out = H.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+def _random_geometries(n, seed):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for k in range(n):
+        ti, tj = rng.uniform(0.3, 5.0, size=2)
+        if k % 4 == 3:  # fully unequal cuboids
+            t = rng.uniform(0.5, 3.0, size=3)
+            s = rng.uniform(0.5, 3.0, size=3)
+        else:
+            t = np.array([2.0, 2.0, ti])
+            s = np.array([2.0, 2.0, tj])
+        R = float(np.exp(rng.uniform(np.log(0.3), np.log(800.0))))
+        d = rng.standard_normal(3)
+        d[2] *= rng.uniform(0.01, 1.0)
+        d *= R / np.linalg.norm(d)
+        X, Y, Z = round(d[0] / 2) * 2.0, round(d[1] / 2) * 2.0, float(d[2])
+        rows.append([X, Y, Z, *t, *s])
+    rows += [[0, 0, 0, 1, 1, 1, 1, 1, 1], [0, 0, 0, 2, 2, 0.5, 2, 2, 0.5], [2, 0, 0, 2, 2, 1, 2, 2, 1],
+             [0, 0, 1.0, 2, 2, 1.0, 2, 2, 0.5], [0, 0, -2.0, 2, 2, 1.0, 2, 2, 2.0]]
+    return np.array(rows, dtype=np.float64)
+
+
+def test_tensor_points_match_oracle():
+    g = _random_geometries(300, seed=11)
+    gt = torch.tensor(g, device="cuda")
+    out = torch.empty(len(g), 6, dtype=torch.float64, device="cuda")
+    dm.demag_tensor_points(gt, out)
+    torch.cuda.synchronize()
+    N = out.cpu().numpy()
+    worst_q = worst_r = 0.0
+    for k, row in enumerate(g):
+        X, Y, Z = row[:3]
+        nq = onw.tensor(X, Y, Z, row[3:6], row[6:9], mode=onw.EXACT_Q)
+        nr = onw.tensor(X, Y, Z, row[3:6], row[6:9], mode=onw.READING_D)
+        sc = np.abs(nq).max()
+        worst_q = max(worst_q, np.abs(N[k] - nq).max() / sc)
+        worst_r = max(worst_r, np.abs(N[k] - nr).max() / sc)
+    assert worst_q < 5e-13, worst_q
+    assert worst_r < 5e-13, worst_r
+    # self term of a cube
+    assert np.allclose(N[len(g) - 5, :3], 1.0 / 3.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("nx,ny,th", [(7, 5, (1.0, 0.5, 2.0)), (4, 9, (0.8,)), (12, 3, (0.6, 3.0))])
+def test_plan_tensor_matches_oracle_spectrum(nx, ny, th):
+    """The stored Fourier tensor equals the oracle's kernels placed on the same
+    padded grid and transformed by numpy's FFT (quadrant, divided by Px Py)."""
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP64)
+    info = plan.info
+    Px, Py, L, npairs = info["Px"], info["Py"], info["L"], info["npairs"]
+    Kx, Qy = Px // 2 + 1, Py // 2 + 1
+    out = torch.empty(Kx * npairs * 6 * Qy, dtype=torch.float64, device="cuda")
+    dm.demag_plan_tensor(plan.handle, out)
+    torch.cuda.synchronize()
+    T = out.cpu().numpy().reshape(Kx, npairs, 6, Qy)
+    plan.close()
+    K = reading_kernels(nx, ny, 2.0, 2.0, tuple(th))
+    pairs = [(i, j) for i in range(L) for j in range(i, L)]
+    qs = np.arange(-(ny - 1), ny) % Py
+    ps = np.arange(-(nx - 1), nx) % Px
+    for P, (i, j) in enumerate(pairs):
+        Kp = np.zeros((6, Py, Px))
+        Kp[:, qs[:, None], ps[None, :]] = K[i, j]
+        S = np.fft.fft2(Kp) / (Px * Py)
+        ref = np.stack([S[0].real, S[1].real, S[2].real, S[3].real, S[4].imag, S[5].imag])
+        # the structure: even components have real spectra, odd ones imaginary
+        assert np.abs(S[:4].imag).max() < 1e-14 and np.abs(S[4:].real).max() < 1e-14
+        ref_q = ref[:, :Qy, :Kx]                     # [component, ky, kx]
+        got_q = np.transpose(T[:, P], (1, 2, 0))     # [kx, component, ky] -> same order
+        sc = np.abs(ref_q).max()
+        assert np.abs(got_q - ref_q).max() < 1e-12 * sc
+
+
+def test_plain32_fp64_matches_direct_sum():
+    """32 x 32 x 3 layers of 1.0 / 0.5 / 2.0 nm, random unit vectors, float64:
+    the GPU field against brute-force summation with the exact _Float128 tensor."""
+    c = inputs.CONFIGS["plain32"]
+    th = tuple(c["thickness"])
+    m = inputs.random_unit_vectors((len(th), c["ny"], c["nx"]), seed=0)
+    Ms = inputs.MS_DEFAULT
+    K = quad_kernels(c["nx"], c["ny"], c["dx"], c["dy"], th)
+    H_ref = odm.direct_sum(K, m, Ms)
+    H = _gpu_field(c["nx"], c["ny"], c["dx"], c["dy"], th, m[None], Ms, dm.PREC_FP64)[0]
+    assert rel_l2(H, H_ref) < TOL64
+
+
+RAGGED = [(7, 5, (1.0, 0.5, 2.0)), (1, 1, (2.0,)), (33, 17, (0.9, 1.3, 0.4, 2.2)), (16, 1, (1.0, 1.0)),
+          (3, 40, (0.7,)), (20, 20, (0.5, 1.5, 0.5, 2.5, 1.0, 0.8, 3.0, 1.1))]
+
+
+@pytest.mark.parametrize("nx,ny,th", RAGGED)
+@pytest.mark.parametrize("prec", [dm.PREC_FP64, dm.PREC_FP32])
+def test_ragged_grids_match_oracle_hybrid(nx, ny, th, prec):
+    m = inputs.random_unit_vectors((len(th), ny, nx), seed=nx * 100 + ny)
+    K = reading_kernels(nx, ny, 2.0, 1.5, th)
+    H_ref = odm.hybrid(K, m, 1.0)
+    H = _gpu_field(nx, ny, 2.0, 1.5, th, m[None], 1.0, prec)[0]
+    assert rel_l2(H, H_ref) < (TOL64 if prec == dm.PREC_FP64 else TOL32)
+
+
+def test_sixteen_layers_fp32():
+    th = tuple(np.round(np.linspace(0.5, 3.0, 16), 3))
+    nx = ny = 24
+    m = inputs.random_unit_vectors((16, ny, nx), seed=21)
+    K = reading_kernels(nx, ny, 2.0, 2.0, th)
+    H_ref = odm.hybrid(K, m, 1.0)
+    H = _gpu_field(nx, ny, 2.0, 2.0, th, m[None], 1.0, dm.PREC_FP32)[0]
+    assert rel_l2(H, H_ref) < TOL32
+
+
+def test_mram256_fp32_full_size():
+    """256 x 256 x 8 MRAM-like stack, float32 apply, the launch the bench times."""
+    c = inputs.CONFIGS["mram256"]
+    th = tuple(c["thickness"])
+    m = inputs.mram_magnetization(c["nx"], c["ny"], len(th), seed=0)
+    K = reading_kernels(c["nx"], c["ny"], c["dx"], c["dy"], th)
+    H_ref = odm.hybrid(K, m, inputs.MS_DEFAULT)
+    H = _gpu_field(c["nx"], c["ny"], c["dx"], c["dy"], th, m[None], inputs.MS_DEFAULT, dm.PREC_FP32)[0]
+    assert rel_l2(H, H_ref) < TOL32
+
+
+def test_batch_states_are_independent():
+    nx, ny, th = 20, 12, (1.0, 0.6, 2.0)
+    m = inputs.random_unit_vectors((3, len(th), ny, nx), seed=31)
+    Hb = _gpu_field(nx, ny, 2.0, 2.0, th, m, 5.0, dm.PREC_FP32)
+    for b in range(3):
+        Hs = _gpu_field(nx, ny, 2.0, 2.0, th, m[b:b + 1], 5.0, dm.PREC_FP32, max_batch=3)[0]
+        assert np.array_equal(Hb[b], Hs)
+
+
+def test_host_entry_point_matches_device():
+    nx, ny, th = 18, 10, (1.0, 0.6, 2.0)
+    m = inputs.random_unit_vectors((2, len(th), ny, nx), seed=41)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP32, max_batch=2)
+    mh = torch.tensor(m, dtype=torch.float32).pin_memory()
+    Hh = torch.empty_like(mh).pin_memory()
+    dm.demag_apply_host(plan.handle, mh, 3.0, Hh)
+    Hd = plan.apply(mh.cuda(), 3.0).cpu()
+    plan.close()
+    assert torch.equal(Hh, Hd)
+
+
+def test_uniform_film_gpu():
+    n, t, Ms = 63, 0.5, 8e5
+    m = np.zeros((1, 1, 3, n, n))
+    m[0, 0, 2] = 1.0
+    H = _gpu_field(n, n, 2.0, 2.0, (t,), m, Ms, dm.PREC_FP64)[0, 0]
+    c = n // 2
+    film = onw.tensor(c * 2.0, c * 2.0, 0.0, (2.0, 2.0, t), (n * 2.0, n * 2.0, t))
+    assert H[2, c, c] == pytest.approx(-Ms * film[2], rel=1e-11)
+
+
+def test_gpu_argument_errors():
+    plan = dm.Plan(8, 8, 2.0, 2.0, (1.0, 2.0), precision=dm.PREC_FP32, max_batch=1)
+    m = torch.zeros(2, 2, 3, 8, 8, device="cuda")
+    with pytest.raises(dm.DemagError) as ei:
+        dm.demag_apply(plan.handle, m, 1.0, torch.empty_like(m), info=plan.info)
+    assert ei.value.status == 1
+    m1 = torch.zeros(1, 2, 3, 8, 8, device="cuda")
+    with pytest.raises(dm.DemagError):
+        dm.demag_apply(plan.handle, m1, 1.0, m1, info=plan.info)
+    with pytest.raises(TypeError):
+        plan.apply(m1.double(), 1.0)
+    plan.close()
