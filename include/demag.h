@@ -176,6 +176,43 @@ demag_status demag_plan_tensor(demag_plan_t plan, void *out, size_t bytes, void 
  */
 demag_status demag_tensor_points(int n, const double *geom, double *out, void *stream);
 
+/*
+ * demag_apply_static - demag_apply for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant of the
+ * same kernels.
+ *
+ * Some callers must not call cudaMalloc while they run: code embedded in a
+ * host framework whose allocator has reserved the GPU's memory (a cudaMalloc
+ * there can fail or fragment that pool), or a time-critical loop that cannot
+ * take the device-wide synchronisation an allocation may cause.  This entry
+ * point allocates nothing.  The caller passes the Fourier tensor (prepared
+ * earlier, e.g. by demag_plan_create + demag_plan_tensor into memory the caller
+ * owns), the layer thicknesses, m and H; the spectrum workspace, twiddle tables
+ * and reciprocity ratios live in one fixed 32 MiB device array inside the
+ * library (held on every GPU that loads the library until the process exits).
+ *
+ *   tensor     DEVICE, layout and values exactly as written by
+ *              demag_plan_tensor for a plan of the same nx, ny, thickness,
+ *              precision (any max_batch)
+ *   thickness  HOST, L layer thicknesses (same as for that plan)
+ *   nx, ny, L, precision   as for demag_plan_create
+ *   m, Ms, H, B, stream    as for demag_apply (no max_batch: the scratch size
+ *              is the limit)
+ *
+ * Scratch needed: B*L*3*(Px/2+1)*ny complex values of the precision plus the
+ * twiddle tables and an L*L ratio table; a request above 32 MiB returns
+ * DEMAG_EUNSUPPORTED with the required size in demag_last_error().
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device); make that first call before any stream capture.  All
+ * calls on a device share the array: calls whose GPU work overlaps (other
+ * streams, other host threads) race on it; calls ordered on one stream do
+ * not.  Nothing in it needs clearing between calls.  The copies of the small
+ * tables from host memory synchronise the stream with earlier work on it.
+ */
+demag_status demag_apply_static(const void *tensor, const double *thickness, int nx, int ny, int L,
+                                int precision, const void *m, double Ms, void *H, int B,
+                                void *stream);
+
 /* demag_destroy - free a plan (NULL is accepted).  Synchronises the device. */
 demag_status demag_destroy(demag_plan_t plan);
 

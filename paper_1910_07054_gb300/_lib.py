@@ -60,6 +60,8 @@ def lib():
     L.demag_plan_tensor.restype = i
     L.demag_tensor_points.argtypes = [i, vp, vp, vp]
     L.demag_tensor_points.restype = i
+    L.demag_apply_static.argtypes = [vp, dp, i, i, i, i, vp, d, vp, i, vp]
+    L.demag_apply_static.restype = i
     L.demag_destroy.argtypes = [vp]
     L.demag_destroy.restype = i
     _lib = L
@@ -178,6 +180,21 @@ def demag_tensor_points(geom, out, stream=None):
                                      ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "demag_tensor_points")
     return out
+
+
+def demag_apply_static(tensor, thickness, nx, ny, precision, m, Ms, H, stream=None):
+    """demag_apply without device allocation: tensor is the device copy written by
+    demag_plan_tensor; the library's fixed scratch array holds the workspace."""
+    info = {"L": len(thickness), "nx": nx, "ny": ny, "precision": precision}
+    B = _field_check(m, info, "m")
+    if _field_check(H, info, "H") != B or H.shape != m.shape:
+        raise ValueError("H must have the shape of m")
+    th = (ctypes.c_double * len(thickness))(*[float(t) for t in thickness])
+    _check(lib().demag_apply_static(ctypes.c_void_p(tensor.data_ptr()), th, int(nx), int(ny),
+                                    len(thickness), int(precision), ctypes.c_void_p(m.data_ptr()),
+                                    float(Ms), ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)),
+           "demag_apply_static")
+    return H
 
 
 def demag_destroy(plan):
