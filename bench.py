@@ -40,6 +40,7 @@ def parse_args():
     p.add_argument("--cpu-budget", type=float, default=20.0,
                    help="seconds of oracle evaluation for the CPU baseline sample")
     p.add_argument("--no-parity", action="store_true", help="skip the oracle field comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return p.parse_args()
 
 
@@ -303,9 +304,10 @@ def run_ours(args):
         H_host = H.double().cpu().numpy()
         rel = None
         cpu = None
-        if not args.no_parity or world == 1:
+        want_cpu = world == 1 and not args.no_cpu
+        if want_cpu or not args.no_parity:
             Khat = oracle_setup(c, th)
-            if world == 1:
+            if want_cpu:
                 times, H_ref = oracle_timed(Khat, m_np, Ms, args.cpu_budget, 1000)
                 cpu = {"value": B / float(np.mean(times)), "unit": "evals/s", "cores": 1, "kind": "oracle",
                        "sample": "%d whole evaluations of the workload, oracle float64 hybrid (numpy "

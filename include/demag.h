@@ -112,6 +112,72 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
                          void *stream);
 
 /*
+ * demag_plan_set_path - choose how the column transforms and the layer
+ * contraction run.
+ *
+ *   path 1: one fused kernel per kx column (the whole column of 3L planes of a
+ *           state in shared memory); possible while 3 * L * (Py + 1) complex
+ *           values fit 220 KB.
+ *   path 2: column FFT, contraction and inverse column FFT as three kernels
+ *           through a [Kx][Py][B][L][3] complex workspace (allocated here on
+ *           first use).
+ *   path 0: the default choice of demag_plan_create (1 when it fits, else 2).
+ * Both paths compute the same field (Eq. FFT_v2); this entry point exists to
+ * test and time them against each other.  Errors: DEMAG_EINVAL, DEMAG_ENOMEM,
+ * DEMAG_EUNSUPPORTED (the path cannot hold this plan).
+ */
+demag_status demag_plan_set_path(demag_plan_t plan, int path);
+
+/*
+ * demag_apply_adjoint - vector-Jacobian product of demag_apply in m.
+ *
+ * demag_apply is linear, H = A m with A_ij = -Ms N(i <- j) (Eq. Hi_discrete),
+ * so the gradient of a loss with respect to m is A^T gH.  The transposed
+ * blocks follow from the target-volume normalisation of the tensor (Sec. 3):
+ * t_i N(i <- j)(d) = t_j N(j <- i)(-d) with symmetric blocks, hence
+ * A^T = D_t A D_t^-1, D_t = diag(layer thickness).  The kernels of
+ * demag_apply run with the source layers scaled by 1/t_j and the target
+ * layers by t_i.
+ *
+ *   gH     DEVICE, [B][L][3][ny][nx], upstream gradient dLoss/dH
+ *   gm     DEVICE, same shape, written: dLoss/dm (must not alias gH)
+ *   other arguments as in demag_apply
+ */
+demag_status demag_apply_adjoint(demag_plan_t plan, const void *gH, double Ms, void *gm, int B,
+                                 void *stream);
+
+/*
+ * demag_apply_dthickness - derivative of the field with respect to one layer
+ * thickness, dH/dt_layer = -Ms sum_j dN(i <- j)/dt_layer m_j.
+ *
+ * t_layer enters N(i <- j) through the target edge (i == layer), the source
+ * edge (j == layer) and the offset z_i - z_j of every pair with exactly one
+ * layer above it.  The derivative tensor of all L*L pairs is evaluated in
+ * double precision on the GPU (Dual-number closed form of Sec. 2 near the
+ * source, the derivative of the far-field volume integral beyond), transformed
+ * like the plan tensor, kept in the plan for the last layer asked for (the
+ * first call for a layer builds it and synchronises `stream`), and applied
+ * with the kernels of demag_apply.
+ *
+ *   m      DEVICE, [B][L][3][ny][nx], read only
+ *   dH     DEVICE, same shape, written (must not alias m)
+ *   layer  0 <= layer < L (0 = bottom layer)
+ */
+demag_status demag_apply_dthickness(demag_plan_t plan, const void *m, double Ms, void *dH, int B,
+                                    int layer, void *stream);
+
+/*
+ * demag_thickness_grad - dLoss/dt_layer = sum over all cells and states of
+ * gH . dH/dt_layer (see demag_apply_dthickness), accumulated in double.
+ *
+ *   m, gH  DEVICE, [B][L][3][ny][nx]
+ *   out    HOST, one double, written
+ * Synchronises `stream`.
+ */
+demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *gH, double Ms, int B,
+                                  int layer, double *out, void *stream);
+
+/*
  * demag_apply_host - demag_apply on HOST buffers (end-to-end call).
  *
  * Copies m from host to the plan's device staging buffer, runs demag_apply,
@@ -141,8 +207,9 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
 /*
  * demag_plan_info - sizes of a plan.
  *
- * out (HOST, 8 values): {nx, ny, L, Px, Py, precision, max_batch,
- *                        number of stored layer pairs}
+ * out (HOST, 10 values): {nx, ny, L, Px, Py, precision, max_batch,
+ *                         number of stored layer pairs, stored row length QyS,
+ *                         column path: 1 fused, 2 split}
  * Px, Py are the padded FFT sizes; the stored tensor holds the layer pairs
  * i <= j (the rest follow from reciprocity, t_i N(i<-j)(d) = t_j N(j<-i)(-d)).
  */
@@ -151,11 +218,16 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
 /*
  * demag_plan_tensor - copy of the stored Fourier-space tensor.
  *
- * out DEVICE, (Px/2+1) * npairs * 6 * (Py/2+1) values of the plan's real type,
- * layout [kx][pair][component][ky] with pair (i <= j) numbered row by row
+ * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,
+ * layout [kx][pair][component][u] with pair (i <= j) numbered row by row
  * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components
  * {Re N_xx, Re N_yy, Re N_zz, Re N_xy, Im N_xz, Im N_yz} of the 2D DFT of
- * N(i <- j) on the padded grid, divided by Px*Py.  bytes is the size of out.
+ * N(i <- j) on the padded grid, divided by Px*Py.  Entry u < Py/2 + 1 holds
+ * the y-frequency ky(u) = min(k, Py - k), k = bitrev(p1(u)) over log2(Py)
+ * bits, where p1(0) = 0, p1(1) = 1 and, for u in [2^(m-1)+1, 2^m+1),
+ * p1(u) = 2^m + u - 2^(m-1) - 1: the order in which a decimation-in-frequency
+ * column transform leaves the spectrum.  Entries u >= Py/2 + 1 (padding up
+ * to QyS, a multiple of 16 bytes) are zero.  bytes is the size of out.
  * Asynchronous on stream.
  */
 demag_status demag_plan_tensor(demag_plan_t plan, void *out, size_t bytes, void *stream);
@@ -191,8 +263,8 @@ demag_status demag_tensor_points(int n, const double *geom, double *out, void *s
  * and reciprocity ratios live in one fixed 32 MiB device array inside the
  * library (held on every GPU that loads the library until the process exits).
  *
- *   tensor     DEVICE, layout and values exactly as written by
- *              demag_plan_tensor for a plan of the same nx, ny, thickness,
+ *   tensor     DEVICE, 16-byte aligned, layout and values exactly as written
+ *              by demag_plan_tensor for a plan of the same nx, ny, thickness,
  *              precision (any max_batch)
  *   thickness  HOST, L layer thicknesses (same as for that plan)
  *   nx, ny, L, precision   as for demag_plan_create
@@ -212,6 +284,18 @@ demag_status demag_tensor_points(int n, const double *geom, double *out, void *s
 demag_status demag_apply_static(const void *tensor, const double *thickness, int nx, int ny, int L,
                                 int precision, const void *m, double Ms, void *H, int B,
                                 void *stream);
+
+/*
+ * demag_tensor_points_dt - the tensor of demag_tensor_points and its
+ * derivative along (dtz, dsz, dZ): the target z-edge, the source z-edge and
+ * the z-offset move at these rates.
+ *
+ *   geom   DEVICE double [n][12]: X, Y, Z, tx, ty, tz, sx, sy, sz, dtz, dsz, dZ
+ *   out    DEVICE double [n][6]: the tensor
+ *   dout   DEVICE double [n][6]: its derivative
+ */
+demag_status demag_tensor_points_dt(int n, const double *geom, double *out, double *dout,
+                                    void *stream);
 
 /* demag_destroy - free a plan (NULL is accepted).  Synchronises the device. */
 demag_status demag_destroy(demag_plan_t plan);

@@ -251,6 +251,54 @@ void oracle_tensor(int mode, double X, double Y, double Z, const double *t, cons
     reading_tensor(X, Y, Z, t, s, out);
 }
 
+/* Derivative of N(target <- source) along (dtz, dsz, dZ) (target z-edge,
+ * source z-edge, z-offset), by a central difference of the exact _Float128
+ * formula with step h: truncation O(h^2), rounding ~1e-34 / h. */
+void oracle_tensor_dt(double X, double Y, double Z, const double *t, const double *s, double dtz,
+                      double dsz, double dZ, double h, double *out)
+{
+    _Float128 hq = h, op[6], om[6];
+    _Float128 tp[3] = {t[0], t[1], (_Float128)t[2] + hq * dtz};
+    _Float128 sp[3] = {s[0], s[1], (_Float128)s[2] + hq * dsz};
+    _Float128 tm[3] = {t[0], t[1], (_Float128)t[2] - hq * dtz};
+    _Float128 sm[3] = {s[0], s[1], (_Float128)s[2] - hq * dsz};
+    gen_tensor_q(X, Y, (_Float128)Z + hq * dZ, tp, sp, 0, op);
+    gen_tensor_q(X, Y, (_Float128)Z - hq * dZ, tm, sm, 0, om);
+    for (int c = 0; c < 6; ++c) out[c] = (double)((op[c] - om[c]) / (2 * hq));
+}
+
+/* d/dt_layer of the layer-pair kernels of oracle_layer_kernels (full offsets),
+ * from oracle_tensor_dt: the target z-edge moves if i == layer, the source
+ * z-edge if j == layer, the offset z_i - z_j by [i > layer] - [j > layer]. */
+void oracle_layer_dkernels(int nx, int ny, double dx, double dy, int L, const double *th, int layer,
+                           double h, double *K)
+{
+    double *z = (double *)malloc((size_t)(L + 1) * sizeof(double));
+    z[0] = 0.0;
+    for (int l = 0; l < L; ++l) z[l + 1] = z[l] + th[l];
+    int PW = 2 * nx - 1, QH = 2 * ny - 1;
+    long long total = (long long)L * L * QH * PW;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long e = 0; e < total; ++e) {
+        int pi = (int)(e % PW);
+        long long r = e / PW;
+        int qi = (int)(r % QH);
+        r /= QH;
+        int j = (int)(r % L);
+        int i = (int)(r / L);
+        double dtz = i == layer, dsz = j == layer, dZ = (double)(i > layer) - (double)(j > layer);
+        double out[6] = {0, 0, 0, 0, 0, 0};
+        if (dtz != 0 || dsz != 0 || dZ != 0) {
+            double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
+            oracle_tensor_dt((pi - (nx - 1)) * dx, (qi - (ny - 1)) * dy, z[i] - z[j], t, s, dtz, dsz,
+                             dZ, h, out);
+        }
+        for (int c = 0; c < 6; ++c)
+            K[((((size_t)i * L + j) * 6 + c) * QH + qi) * PW + pi] = out[c];
+    }
+    free(z);
+}
+
 /* f and g with a double-double split of the _Float128 value (hi + lo). */
 void oracle_newell_fg_q(int which, double x, double y, double z, double *hi, double *lo)
 {

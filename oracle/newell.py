@@ -38,6 +38,13 @@ def lib():
         L.oracle_layer_kernels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, dp]
         L.oracle_layer_kernels.restype = None
+        L.oracle_tensor_dt.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, dp]
+        L.oracle_tensor_dt.restype = None
+        L.oracle_layer_dkernels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, dp]
+        L.oracle_layer_dkernels.restype = None
         _lib = L
     return _lib
 
@@ -102,4 +109,25 @@ def layer_kernels(nx, ny, dx, dy, thickness, mode=READING_D, full=True):
     K = np.zeros(shape)
     lib().oracle_layer_kernels(int(mode), int(nx), int(ny), float(dx), float(dy), int(L), _dp(th),
                                1 if full else 0, _dp(K))
+    return K
+
+
+def tensor_dt(X, Y, Z, target, source, dtz, dsz, dZ, h=1e-9):
+    """d N(target <- source) along (target z-edge, source z-edge, z-offset),
+    central difference of the exact _Float128 tensor with step h."""
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    s = np.ascontiguousarray(source, dtype=np.float64)
+    out = np.zeros(6)
+    lib().oracle_tensor_dt(float(X), float(Y), float(Z), _dp(t), _dp(s), float(dtz), float(dsz),
+                           float(dZ), float(h), _dp(out))
+    return out
+
+
+def layer_dkernels(nx, ny, dx, dy, thickness, layer, h=1e-9):
+    """d/d t_layer of layer_kernels(full=True) (exact tensor, _Float128 differences)."""
+    th = np.ascontiguousarray(thickness, dtype=np.float64)
+    L = th.size
+    K = np.zeros((L, L, 6, 2 * ny - 1, 2 * nx - 1))
+    lib().oracle_layer_dkernels(int(nx), int(ny), float(dx), float(dy), int(L), _dp(th), int(layer),
+                                float(h), _dp(K))
     return K

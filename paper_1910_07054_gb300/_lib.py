@@ -60,6 +60,16 @@ def lib():
     L.demag_plan_tensor.restype = i
     L.demag_tensor_points.argtypes = [i, vp, vp, vp]
     L.demag_tensor_points.restype = i
+    L.demag_plan_set_path.argtypes = [vp, i]
+    L.demag_plan_set_path.restype = i
+    L.demag_apply_adjoint.argtypes = [vp, vp, d, vp, i, vp]
+    L.demag_apply_adjoint.restype = i
+    L.demag_apply_dthickness.argtypes = [vp, vp, d, vp, i, i, vp]
+    L.demag_apply_dthickness.restype = i
+    L.demag_thickness_grad.argtypes = [vp, vp, vp, d, i, i, dp, vp]
+    L.demag_thickness_grad.restype = i
+    L.demag_tensor_points_dt.argtypes = [i, vp, vp, vp, vp]
+    L.demag_tensor_points_dt.restype = i
     L.demag_apply_static.argtypes = [vp, dp, i, i, i, i, vp, d, vp, i, vp]
     L.demag_apply_static.restype = i
     L.demag_destroy.argtypes = [vp]
@@ -101,9 +111,9 @@ def demag_plan_create(nx, ny, dx, dy, thickness, precision=PREC_FP32, max_batch=
 
 
 def demag_plan_info(plan):
-    out = (ctypes.c_longlong * 8)()
+    out = (ctypes.c_longlong * 10)()
     _check(lib().demag_plan_info(ctypes.c_void_p(plan), out), "demag_plan_info")
-    keys = ("nx", "ny", "L", "Px", "Py", "precision", "max_batch", "npairs")
+    keys = ("nx", "ny", "L", "Px", "Py", "precision", "max_batch", "npairs", "QyS", "path")
     return dict(zip(keys, [int(v) for v in out]))
 
 
@@ -135,6 +145,62 @@ def demag_apply(plan, m, Ms, H, stream=None, info=None):
     _check(lib().demag_apply(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
                              ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)), "demag_apply")
     return H
+
+
+def demag_plan_set_path(plan, path):
+    """1: fused column kernel, 2: split column kernels, 0: the plan's default."""
+    _check(lib().demag_plan_set_path(ctypes.c_void_p(plan), int(path)), "demag_plan_set_path")
+
+
+def demag_apply_adjoint(plan, gH, Ms, gm, stream=None, info=None):
+    """gm <- A^T gH, the vector-Jacobian product of demag_apply in m."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(gH, info, "gH")
+    if _field_check(gm, info, "gm") != B or gm.shape != gH.shape:
+        raise ValueError("gm must have the shape of gH")
+    _check(lib().demag_apply_adjoint(ctypes.c_void_p(plan), ctypes.c_void_p(gH.data_ptr()), float(Ms),
+                                     ctypes.c_void_p(gm.data_ptr()), int(B), _stream(stream)),
+           "demag_apply_adjoint")
+    return gm
+
+
+def demag_apply_dthickness(plan, m, Ms, dH, layer, stream=None, info=None):
+    """dH <- dH/dt_layer for the states m."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(m, info, "m")
+    if _field_check(dH, info, "dH") != B or dH.shape != m.shape:
+        raise ValueError("dH must have the shape of m")
+    _check(lib().demag_apply_dthickness(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
+                                        ctypes.c_void_p(dH.data_ptr()), int(B), int(layer),
+                                        _stream(stream)), "demag_apply_dthickness")
+    return dH
+
+
+def demag_thickness_grad(plan, m, gH, Ms, layer, stream=None, info=None):
+    """sum(gH * dH/dt_layer) as a float (synchronises)."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(m, info, "m")
+    if _field_check(gH, info, "gH") != B or gH.shape != m.shape:
+        raise ValueError("gH must have the shape of m")
+    out = ctypes.c_double()
+    _check(lib().demag_thickness_grad(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()),
+                                      ctypes.c_void_p(gH.data_ptr()), float(Ms), int(B), int(layer),
+                                      ctypes.byref(out), _stream(stream)), "demag_thickness_grad")
+    return out.value
+
+
+def demag_tensor_points_dt(geom, out, dout, stream=None):
+    """geom: CUDA float64 [n, 12]; out, dout: CUDA float64 [n, 6]."""
+    import torch
+    for t in (geom, out, dout):
+        if t.dtype != torch.float64 or not t.is_cuda:
+            raise TypeError("geom, out and dout must be CUDA float64 tensors")
+    if geom.shape[-1] != 12 or out.shape[-1] != 6 or dout.shape != out.shape or geom.shape[0] != out.shape[0]:
+        raise ValueError("geom must be [n, 12], out and dout [n, 6]")
+    _check(lib().demag_tensor_points_dt(int(geom.shape[0]), ctypes.c_void_p(geom.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(dout.data_ptr()),
+                                        _stream(stream)), "demag_tensor_points_dt")
+    return out, dout
 
 
 def demag_apply_timed(plan, m, Ms, H, stream=None, info=None):

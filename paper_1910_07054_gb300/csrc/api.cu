@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "layout.cuh"
 
 namespace demag {
 
@@ -54,6 +55,11 @@ static void free_plan(demag_plan *p) {
     cudaFree(p->d_spec);
     cudaFree(p->d_stage_m);
     cudaFree(p->d_stage_H);
+    cudaFree(p->d_spec2);
+    cudaFree(p->d_tscale);
+    cudaFree(p->d_dtensor);
+    cudaFree(p->d_dH);
+    cudaFree(p->d_dot);
     delete p;
 }
 
@@ -76,7 +82,9 @@ static demag_status dalloc(void **ptr, size_t bytes, const char *what) {
         if (s_ != DEMAG_OK) return s_;        \
     } while (0)
 
-static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
+// Builds the plan tensor (layer < 0: pairs i <= j of N) or the derivative
+// tensor d N / d t_layer (all L*L pairs) into dst.
+static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void *dst) {
     const int L = p->L;
     std::vector<int> pi, pj;
     for (int i = 0; i < L; ++i)
@@ -84,6 +92,7 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
             pi.push_back(i);
             pj.push_back(j);
         }
+    const int npairs = layer < 0 ? p->npairs : L * L;
     std::vector<double> z(L + 1, 0.0);
     for (int l = 0; l < L; ++l) z[l + 1] = z[l] + p->thickness[l];
 
@@ -95,7 +104,7 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
         size_t budget = (size_t)4 << 30;
         size_t c = budget / plane_bytes;
         if (c < 1) c = 1;
-        if (c > (size_t)p->npairs) c = p->npairs;
+        if (c > (size_t)npairs) c = npairs;
         chunk = (int)c;
     }
     int *d_pi = nullptr, *d_pj = nullptr;
@@ -130,14 +139,17 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
             rc = cuda_fail(e, "cudaMemcpyAsync(tensor set-up)");
             break;
         }
-        for (int p0 = 0; p0 < p->npairs && rc == DEMAG_OK; p0 += chunk) {
-            const int np = std::min(chunk, p->npairs - p0);
+        for (int p0 = 0; p0 < npairs && rc == DEMAG_OK; p0 += chunk) {
+            const int np = std::min(chunk, npairs - p0);
             if ((e = cudaMemsetAsync(planes, 0, plane_bytes * np, st)) != cudaSuccess) {
                 rc = cuda_fail(e, "cudaMemsetAsync(tensor planes)");
                 break;
             }
-            if ((e = launch_kernel_planes(planes, p0, np, d_pi, d_pj, p->nx, p->ny, p->dx, p->dy,
-                                          p->log2Px, p->log2Py, d_z, d_th, st)) != cudaSuccess) {
+            e = layer < 0 ? launch_kernel_planes(planes, p0, np, d_pi, d_pj, p->nx, p->ny, p->dx, p->dy,
+                                                 p->log2Px, p->log2Py, d_z, d_th, st)
+                          : launch_dkernel_planes(planes, p0, np, L, layer, p->nx, p->ny, p->dx, p->dy,
+                                                  p->log2Px, p->log2Py, d_z, d_th, st);
+            if (e != cudaSuccess) {
                 rc = cuda_fail(e, "tensor evaluation kernel");
                 break;
             }
@@ -146,8 +158,8 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
                 rc = cuda_fail(e, "tensor FFT kernels");
                 break;
             }
-            if ((e = launch_extract_tensor(planes, p0, np, p->npairs, p->log2Px, p->log2Py,
-                                           p->d_tensor, p->precision == DEMAG_PREC_FP64, st)) !=
+            if ((e = launch_extract_tensor(planes, p0, np, npairs, p->log2Px, p->log2Py, p->QyS,
+                                           dst, p->precision == DEMAG_PREC_FP64, st)) !=
                 cudaSuccess) {
                 rc = cuda_fail(e, "tensor extraction kernel");
                 break;
@@ -158,6 +170,37 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st) {
     } while (0);
     cleanup();
     return rc;
+}
+
+// sum_i a[i] * b[i] accumulated in double into *out (zeroed beforehand)
+template <typename T>
+__global__ void k_dot(const T *__restrict__ a, const T *__restrict__ b, size_t n, double *out) {
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+
+static demag_status ensure_dtensor(demag_plan *p, int layer, cudaStream_t st) {
+    if (p->dlayer == layer) return DEMAG_OK;
+    const size_t real = p->precision == DEMAG_PREC_FP64 ? 8 : 4;
+    const size_t bytes = (size_t)p->Kx * p->L * p->L * 6 * p->QyS * real;
+    if (!p->d_dtensor) {
+        DEMAG_TRY(dalloc(&p->d_dtensor, bytes, "derivative tensor"));
+    }
+    DEMAG_CUDA(cudaMemsetAsync(p->d_dtensor, 0, bytes, st));
+    p->dlayer = -1;
+    DEMAG_TRY(build_tensor(p, st, layer, p->d_dtensor));
+    p->dlayer = layer;
+    return DEMAG_OK;
 }
 
 }  // namespace demag
@@ -216,11 +259,13 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     if (p->log2Py < 2) p->log2Py = 2;
     p->Kx = (1 << p->log2Px) / 2 + 1;
     p->Qy = (1 << p->log2Py) / 2 + 1;
+    p->QyS = tensor_row(p->log2Py, precision == DEMAG_PREC_FP64);
     p->npairs = L * (L + 1) / 2;
     const bool fp64 = precision == DEMAG_PREC_FP64;
-    if (L > fused_max_layers(fp64, p->log2Py)) {
+    p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
+    if (p->split && !split_supported(L, max_batch, fp64)) {
         delete p;
-        return fail(DEMAG_EUNSUPPORTED, "layer count above the fused contraction limit for this grid");
+        return fail(DEMAG_EUNSUPPORTED, "layer count x batch above the contraction kernels' limits");
     }
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&p->device);
@@ -231,22 +276,34 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     demag_status rc = upload_gauss_legendre();
     const size_t real = fp64 ? sizeof(double) : sizeof(float);
     const size_t cpx = 2 * real;
-    p->tensor_bytes = (size_t)p->Kx * p->npairs * 6 * p->Qy * real;
+    p->tensor_bytes = (size_t)p->Kx * p->npairs * 6 * p->QyS * real;
     p->field_bytes_per_state = (size_t)L * 3 * ny * nx * real;
     if (rc == DEMAG_OK) rc = dalloc(&p->d_tensor, p->tensor_bytes, "tensor");
+    if (rc == DEMAG_OK && (e = cudaMemset(p->d_tensor, 0, p->tensor_bytes)) != cudaSuccess)
+        rc = cuda_fail(e, "cudaMemset(tensor)");
     if (rc == DEMAG_OK) rc = dalloc(&p->d_ratio, (size_t)L * L * real, "ratios");
     if (rc == DEMAG_OK) rc = dalloc(&p->d_twx, (size_t)(1 << p->log2Px) / 2 * cpx, "twiddles");
     if (rc == DEMAG_OK) rc = dalloc(&p->d_twy, (size_t)(1 << p->log2Py) / 2 * cpx, "twiddles");
     if (rc == DEMAG_OK)
         rc = dalloc(&p->d_spec, (size_t)max_batch * L * 3 * p->Kx * ny * cpx, "spectrum workspace");
+    if (rc == DEMAG_OK && p->split)
+        rc = dalloc(&p->d_spec2, split_workspace_bytes(L, max_batch, p->log2Px, p->log2Py, fp64),
+                    "column workspace");
+    if (rc == DEMAG_OK) rc = dalloc(&p->d_tscale, (size_t)2 * L * real, "layer scales");
     if (rc == DEMAG_OK) {
         // t_j / t_i for target i, source j (reciprocity of the stored pairs)
         std::vector<double> r64((size_t)L * L);
         for (int i = 0; i < L; ++i)
             for (int j = 0; j < L; ++j) r64[(size_t)i * L + j] = thickness[j] / thickness[i];
         auto tx64 = twiddles<double2>(p->log2Px), ty64 = twiddles<double2>(p->log2Py);
+        std::vector<double> sc64(2 * L);
+        for (int l = 0; l < L; ++l) {
+            sc64[l] = thickness[l];            // t_l
+            sc64[L + l] = 1.0 / thickness[l];  // 1 / t_l
+        }
         if (fp64) {
-            if ((e = cudaMemcpy(p->d_ratio, r64.data(), r64.size() * 8, cudaMemcpyHostToDevice)) ||
+            if ((e = cudaMemcpy(p->d_tscale, sc64.data(), sc64.size() * 8, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy(p->d_ratio, r64.data(), r64.size() * 8, cudaMemcpyHostToDevice)) ||
                 (e = cudaMemcpy(p->d_twx, tx64.data(), tx64.size() * 16, cudaMemcpyHostToDevice)) ||
                 (e = cudaMemcpy(p->d_twy, ty64.data(), ty64.size() * 16, cudaMemcpyHostToDevice)))
                 rc = cuda_fail(e, "cudaMemcpy(plan constants)");
@@ -255,13 +312,15 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
             std::vector<float2> tx32(tx64.size()), ty32(ty64.size());
             for (size_t k = 0; k < tx64.size(); ++k) tx32[k] = make_float2((float)tx64[k].x, (float)tx64[k].y);
             for (size_t k = 0; k < ty64.size(); ++k) ty32[k] = make_float2((float)ty64[k].x, (float)ty64[k].y);
-            if ((e = cudaMemcpy(p->d_ratio, r32.data(), r32.size() * 4, cudaMemcpyHostToDevice)) ||
+            std::vector<float> sc32(sc64.begin(), sc64.end());
+            if ((e = cudaMemcpy(p->d_tscale, sc32.data(), sc32.size() * 4, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy(p->d_ratio, r32.data(), r32.size() * 4, cudaMemcpyHostToDevice)) ||
                 (e = cudaMemcpy(p->d_twx, tx32.data(), tx32.size() * 8, cudaMemcpyHostToDevice)) ||
                 (e = cudaMemcpy(p->d_twy, ty32.data(), ty32.size() * 8, cudaMemcpyHostToDevice)))
                 rc = cuda_fail(e, "cudaMemcpy(plan constants)");
         }
     }
-    if (rc == DEMAG_OK) rc = build_tensor(p, st);
+    if (rc == DEMAG_OK) rc = build_tensor(p, st, -1, p->d_tensor);
     if (rc != DEMAG_OK) {
         free_plan(p);
         return rc;
@@ -288,6 +347,7 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.log2Px = plan->log2Px;
     a.log2Py = plan->log2Py;
     a.npairs = plan->npairs;
+    a.QyS = plan->QyS;
     a.tensor = plan->d_tensor;
     a.ratio = plan->d_ratio;
     a.twx = plan->d_twx;
@@ -295,6 +355,8 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.log2twx = plan->log2Px;
     a.log2twy = plan->log2Py;
     a.spec = plan->d_spec;
+    a.spec2 = plan->d_spec2;
+    a.split = plan->split;
     a.Ms = Ms;
     return a;
 }
@@ -349,6 +411,88 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
     return DEMAG_OK;
 }
 
+demag_status demag_plan_set_path(demag_plan_t plan, int path) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    const bool fp64 = plan->precision == DEMAG_PREC_FP64;
+    if (path == 0) path = plan->L > fused_max_layers(fp64, plan->log2Py) ? 2 : 1;
+    if (path == 1) {
+        if (plan->L > fused_max_layers(fp64, plan->log2Py))
+            return fail(DEMAG_EUNSUPPORTED, "the fused kernel cannot hold this stack's columns");
+        plan->split = 0;
+        return DEMAG_OK;
+    }
+    if (path != 2) return fail(DEMAG_EINVAL, "path must be 0, 1 or 2");
+    if (!split_supported(plan->L, plan->max_batch, fp64))
+        return fail(DEMAG_EUNSUPPORTED, "layer count x batch above the split kernels' limits");
+    if (!plan->d_spec2)
+        DEMAG_TRY(dalloc(&plan->d_spec2,
+                         split_workspace_bytes(plan->L, plan->max_batch, plan->log2Px, plan->log2Py, fp64),
+                         "column workspace"));
+    plan->split = 1;
+    return DEMAG_OK;
+}
+
+demag_status demag_apply_adjoint(demag_plan_t plan, const void *gH, double Ms, void *gm, int B,
+                                 void *stream) {
+    demag_status rc = check_apply(plan, gH, Ms, gm, B);
+    if (rc != DEMAG_OK) return rc;
+    ApplyArgs a = apply_args(plan, Ms, B);
+    const size_t real = plan->precision == DEMAG_PREC_FP64 ? 8 : 4;
+    a.in_scale = (const char *)plan->d_tscale + plan->L * real;  // 1 / t_j on the sources
+    a.out_scale = plan->d_tscale;                               // t_i on the targets
+    cudaError_t e = launch_apply(a, gH, gm, plan->precision == DEMAG_PREC_FP64, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "demag_apply_adjoint kernels");
+    return DEMAG_OK;
+}
+
+demag_status demag_apply_dthickness(demag_plan_t plan, const void *m, double Ms, void *dH, int B,
+                                    int layer, void *stream) {
+    demag_status rc = check_apply(plan, m, Ms, dH, B);
+    if (rc != DEMAG_OK) return rc;
+    if (layer < 0 || layer >= plan->L) return fail(DEMAG_EINVAL, "layer out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    DEMAG_TRY(ensure_dtensor(plan, layer, st));
+    ApplyArgs a = apply_args(plan, Ms, B);
+    a.tensor = plan->d_dtensor;
+    a.npairs = plan->L * plan->L;
+    a.full_pairs = 1;
+    cudaError_t e = launch_apply(a, m, dH, plan->precision == DEMAG_PREC_FP64, st);
+    if (e != cudaSuccess) return cuda_fail(e, "demag_apply_dthickness kernels");
+    return DEMAG_OK;
+}
+
+demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *gH, double Ms, int B,
+                                  int layer, double *out, void *stream) {
+    if (!out) return fail(DEMAG_EINVAL, "out is NULL");
+    if (!gH) return fail(DEMAG_EINVAL, "gH is NULL");
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!plan->d_dH) DEMAG_TRY(dalloc(&plan->d_dH, plan->field_bytes_per_state * plan->max_batch, "dH/dt"));
+    if (!plan->d_dot) DEMAG_TRY(dalloc((void **)&plan->d_dot, sizeof(double), "reduction"));
+    DEMAG_TRY(demag_apply_dthickness(plan, m, Ms, plan->d_dH, B, layer, stream));
+    DEMAG_CUDA(cudaMemsetAsync(plan->d_dot, 0, sizeof(double), st));
+    const size_t n = plan->field_bytes_per_state / (plan->precision == DEMAG_PREC_FP64 ? 8 : 4) * B;
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 1024);
+    if (plan->precision == DEMAG_PREC_FP64)
+        k_dot<double><<<grid, 256, 0, st>>>((const double *)gH, (const double *)plan->d_dH, n, plan->d_dot);
+    else
+        k_dot<float><<<grid, 256, 0, st>>>((const float *)gH, (const float *)plan->d_dH, n, plan->d_dot);
+    DEMAG_CUDA(cudaGetLastError());
+    DEMAG_CUDA(cudaMemcpyAsync(out, plan->d_dot, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(cudaStreamSynchronize(st));
+    return DEMAG_OK;
+}
+
+demag_status demag_tensor_points_dt(int n, const double *geom, double *out, double *dout,
+                                    void *stream) {
+    if (n < 0) return fail(DEMAG_EINVAL, "n must be >= 0");
+    if (n > 0 && (!geom || !out || !dout)) return fail(DEMAG_EINVAL, "geom, out or dout is NULL");
+    DEMAG_TRY(upload_gauss_legendre());
+    cudaError_t e = launch_tensor_points_dt(n, geom, out, dout, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor derivative points kernel");
+    return DEMAG_OK;
+}
+
 demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     if (!plan || !out) return fail(DEMAG_EINVAL, "plan or out is NULL");
     out[0] = plan->nx;
@@ -359,6 +503,8 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     out[5] = plan->precision;
     out[6] = plan->max_batch;
     out[7] = plan->npairs;
+    out[8] = plan->QyS;
+    out[9] = plan->split ? 2 : 1;
     return DEMAG_OK;
 }
 

@@ -40,30 +40,52 @@ cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pai
                                  int log2Px, int log2Py, const double *z, const double *th,
                                  cudaStream_t st);
 
+// Tensor and its derivative along (dtz, dsz, dZ) at geom[n][12]
+// (X,Y,Z,tx,ty,tz,sx,sy,sz,dtz,dsz,dZ) -> out[n][6], dout[n][6].
+cudaError_t launch_tensor_points_dt(int n, const double *geom, double *out, double *dout,
+                                    cudaStream_t st);
+
+// d N(i <- j)/d t_layer of all L*L pairs P = i*L + j in [p0, p0 + np), as
+// three complex planes per pair like launch_kernel_planes (zeroed beforehand).
+cudaError_t launch_dkernel_planes(double2 *planes, int p0, int np, int L, int layer, int nx, int ny,
+                                  double dx, double dy, int log2Px, int log2Py, const double *z,
+                                  const double *th, cudaStream_t st);
+
 // In-place 2D FFT (forward, double) of nplanes planes [Py][Px].
 cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log2Py,
                                const double2 *twx, int log2twx, const double2 *twy, int log2twy,
                                cudaStream_t st);
 
 // Extract the stored quadrant of pairs [p0, p0+np) from transformed planes into
-// the plan tensor [Kx][npairs][6][Qy] (float or double), scaled by 1/(Px Py).
+// the plan tensor [Kx][npairs][6][QyS] (float or double), scaled by 1/(Px Py),
+// y-frequencies in the stored order of layout.cuh.
 cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs,
-                                  int log2Px, int log2Py, void *tensor, bool fp64,
+                                  int log2Px, int log2Py, int QyS, void *tensor, bool fp64,
                                   cudaStream_t st);
 
 // ---- apply ---------------------------------------------------------------
 struct ApplyArgs {
     int nx, ny, L, B;
     int log2Px, log2Py;
-    int npairs;
-    const void *tensor;   // [Kx][npairs][6][Qy]
+    int npairs, QyS;
+    const void *tensor;   // [Kx][npairs][6][QyS]
     const void *ratio;    // [L][L]: t_j / t_i (plan real type)
     const void *twx;      // twiddles for Px (complex of the plan type)
     const void *twy;      // twiddles for Py
     int log2twx, log2twy;
     void *spec;           // [B][L][3][Kx][ny] complex workspace
+    void *spec2 = nullptr;  // split path: [Kx][Py][B][L][3] complex workspace
+    int split = 0;        // 1: column transforms and contraction in separate kernels
+    int full_pairs = 0;   // 1: tensor holds all L*L pairs (no reciprocity)
+    const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
+    const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
     double Ms;
 };
+
+// Split path (apply_split.cu).
+size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);
+bool split_supported(int L, int B, bool fp64);
+cudaError_t launch_split_columns(const ApplyArgs &a, bool fp64, cudaStream_t st);
 
 // Largest layer count the fused column kernel handles for a precision.
 int fused_max_layers(bool fp64, int log2Py);
@@ -77,12 +99,19 @@ cudaError_t launch_apply(const ApplyArgs &a, const void *m, void *H, bool fp64, 
 struct demag_plan {
     int nx, ny, L, precision, max_batch;
     double dx, dy;
-    int log2Px, log2Py, Kx, Qy, npairs;
+    int log2Px, log2Py, Kx, Qy, QyS, npairs;
     std::vector<double> thickness;
-    void *d_tensor = nullptr;     // [Kx][npairs][6][Qy]
+    void *d_tensor = nullptr;     // [Kx][npairs][6][QyS]
     void *d_ratio = nullptr;      // [L][L]
     void *d_twx = nullptr, *d_twy = nullptr;
     void *d_spec = nullptr;       // [max_batch][L][3][Kx][ny] complex
+    void *d_spec2 = nullptr;      // split path workspace
+    int split = 0;                // 1: split path
+    void *d_tscale = nullptr;     // [2L]: t_l, then 1 / t_l (plan real type)
+    void *d_dtensor = nullptr;    // d N / d t_dlayer, all L*L pairs, [Kx][L*L][6][QyS]
+    int dlayer = -1;              // layer of d_dtensor (-1: none)
+    void *d_dH = nullptr;         // [max_batch] fields of d H / d t
+    double *d_dot = nullptr;      // reduction scratch
     void *d_stage_m = nullptr;    // staging for demag_apply_host
     void *d_stage_H = nullptr;
     size_t tensor_bytes = 0, field_bytes_per_state = 0;

@@ -22,6 +22,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "layout.cuh"
 
 namespace demag {
 
@@ -74,32 +75,68 @@ demag_status upload_gauss_legendre() {
 }
 
 // ---- closed form (Sec. 2) ------------------------------------------------
+//
+// Written once for a scalar type S: double, or Dual (value and first
+// derivative along one direction of the arguments) for d/dt of the tensor.
+
+struct Dual {
+    double v, d;
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+    const double q = a.v / b.v;
+    return {q, (a.d - q * b.d) / b.v};
+}
+__device__ __forceinline__ Dual operator/(Dual a, double b) { return {a.v / b, a.d / b}; }
+__device__ __forceinline__ Dual &operator+=(Dual &a, Dual b) { a = a + b; return a; }
+__device__ __forceinline__ Dual &operator-=(Dual &a, Dual b) { a = a - b; return a; }
+
+__device__ __forceinline__ double val(double a) { return a; }
+__device__ __forceinline__ double val(Dual a) { return a.v; }
+__device__ __forceinline__ double s_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ Dual s_sqrt(Dual a) {
+    const double r = sqrt(a.v);
+    return {r, r > 0.0 ? a.d / (2.0 * r) : 0.0};
+}
+__device__ __forceinline__ double s_asinh(double a) { return asinh(a); }
+__device__ __forceinline__ Dual s_asinh(Dual a) { return {asinh(a.v), a.d / sqrt(1.0 + a.v * a.v)}; }
+__device__ __forceinline__ double s_atan(double a) { return atan(a); }
+__device__ __forceinline__ Dual s_atan(Dual a) { return {atan(a.v), a.d / (1.0 + a.v * a.v)}; }
+template <typename S> __device__ __forceinline__ S s_const(double c);
+template <> __device__ __forceinline__ double s_const<double>(double c) { return c; }
+template <> __device__ __forceinline__ Dual s_const<Dual>(double c) { return {c, 0.0}; }
 
 // Newell f: d^2/dy^2 d^2/dz^2 f = 1/R.  Products with a vanishing prefactor
-// are dropped (their limit is zero).
-__device__ __noinline__ double newell_f(double x, double y, double z) {
-    const double x2 = x * x, y2 = y * y, z2 = z * z;
-    const double R = sqrt(x2 + y2 + z2);
-    double v = (2.0 * x2 - y2 - z2) * R / 6.0;
-    const double xz = x2 + z2, xy = x2 + y2;
-    if (y != 0.0 && xz > 0.0) v += 0.5 * y * (z2 - x2) * asinh(y / sqrt(xz));
-    if (z != 0.0 && xy > 0.0) v += 0.5 * z * (y2 - x2) * asinh(z / sqrt(xy));
-    if (x != 0.0 && y != 0.0 && z != 0.0) v -= x * y * z * atan(y * z / (x * R));
+// are dropped (their limit, and that of their derivative, is zero).
+template <typename S>
+__device__ __noinline__ S newell_f(S x, S y, S z) {
+    const S x2 = x * x, y2 = y * y, z2 = z * z;
+    const S R = s_sqrt(x2 + y2 + z2);
+    S v = (2.0 * x2 - y2 - z2) * R / 6.0;
+    const S xz = x2 + z2, xy = x2 + y2;
+    if (val(y) != 0.0 && val(xz) > 0.0) v += 0.5 * (y * (z2 - x2) * s_asinh(y / s_sqrt(xz)));
+    if (val(z) != 0.0 && val(xy) > 0.0) v += 0.5 * (z * (y2 - x2) * s_asinh(z / s_sqrt(xy)));
+    if (val(x) != 0.0 && val(y) != 0.0 && val(z) != 0.0) v -= x * y * z * s_atan(y * z / (x * R));
     return v;
 }
 
 // Newell g: d/dx d/dy d^2/dz^2 g = 1/R.
-__device__ __noinline__ double newell_g(double x, double y, double z) {
-    const double x2 = x * x, y2 = y * y, z2 = z * z;
-    const double R = sqrt(x2 + y2 + z2);
-    double v = -x * y * R / 3.0;
-    if (y != 0.0) v += y / 6.0 * (3.0 * z2 - y2) * asinh(x / sqrt(y2 + z2));
-    if (x != 0.0) v += x / 6.0 * (3.0 * z2 - x2) * asinh(y / sqrt(x2 + z2));
-    if (x != 0.0 && y != 0.0 && z != 0.0) {
-        v += x * y * z * asinh(z / sqrt(x2 + y2));
-        v -= z2 * z / 6.0 * atan(x * y / (z * R));
-        v -= 0.5 * z * y2 * atan(x * z / (y * R));
-        v -= 0.5 * z * x2 * atan(y * z / (x * R));
+template <typename S>
+__device__ __noinline__ S newell_g(S x, S y, S z) {
+    const S x2 = x * x, y2 = y * y, z2 = z * z;
+    const S R = s_sqrt(x2 + y2 + z2);
+    S v = -(x * y * R) / 3.0;
+    if (val(y) != 0.0) v += y * (3.0 * z2 - y2) * s_asinh(x / s_sqrt(y2 + z2)) / 6.0;
+    if (val(x) != 0.0) v += x * (3.0 * z2 - x2) * s_asinh(y / s_sqrt(x2 + z2)) / 6.0;
+    if (val(x) != 0.0 && val(y) != 0.0 && val(z) != 0.0) {
+        v += x * y * z * s_asinh(z / s_sqrt(x2 + y2));
+        v -= z2 * z * s_atan(x * y / (z * R)) / 6.0;
+        v -= 0.5 * (z * y2 * s_atan(x * z / (y * R)));
+        v -= 0.5 * (z * x2 * s_atan(y * z / (x * R)));
     }
     return v;
 }
@@ -107,66 +144,68 @@ __device__ __noinline__ double newell_g(double x, double y, double z) {
 constexpr double kPi = 3.14159265358979323846;
 
 // N_xx: x-face pairs (Eq. Nxx) x F split into F_1 (y) and F_2 (z) (App. A).
-__device__ __noinline__ double closed_nxx(double X, double Y, double Z, double tx, double ty, double tz,
-                             double sx, double sy, double sz) {
-    const double sxa[4] = {0.0, tx, -sx, tx - sx};
-    const double sya[4] = {ty, 0.0, ty - sy, -sy};
-    const double sza[4] = {tz, 0.0, tz - sz, -sz};
-    double acc = 0.0;
+template <typename S>
+__device__ __noinline__ S closed_nxx(S X, S Y, S Z, S tx, S ty, S tz, S sx, S sy, S sz) {
+    const S zero = s_const<S>(0.0);
+    const S sxa[4] = {zero, tx, -sx, tx - sx};
+    const S sya[4] = {ty, zero, ty - sy, -sy};
+    const S sza[4] = {tz, zero, tz - sz, -sz};
+    S acc = zero;
 #pragma unroll 1
     for (int a = 0; a < 4; ++a) {
-        double ya = 0.0;
+        S ya = zero;
 #pragma unroll 1
         for (int b = 0; b < 4; ++b) {
-            double zb = 0.0;
+            S zb = zero;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
-                const double v = newell_f(X + sxa[a], Y + sya[b], Z + sza[c]);
-                zb += (c == 0 || c == 3) ? v : -v;
+                const S v = newell_f<S>(X + sxa[a], Y + sya[b], Z + sza[c]);
+                if (c == 0 || c == 3) zb += v; else zb -= v;
             }
-            ya += (b == 0 || b == 3) ? zb : -zb;
+            if (b == 0 || b == 3) ya += zb; else ya -= zb;
         }
-        acc += (a == 0 || a == 3) ? ya : -ya;
+        if (a == 0 || a == 3) acc += ya; else acc -= ya;
     }
-    return acc / (4.0 * kPi * tx * ty * tz);
+    return acc / (4.0 * kPi * (tx * ty * tz));
 }
 
 // N_xy: target/source face pairs of Eq. Nxy (fourth term at Y + Delta y) x G
 // split over x and y (App. B) x G_1 over z.
-__device__ __noinline__ double closed_nxy(double X, double Y, double Z, double tx, double ty, double tz,
-                             double sx, double sy, double sz) {
-    const double sxa[4] = {tx, 0.0, tx - sx, -sx};
-    const double sya[4] = {0.0, -sy, ty, ty - sy};
-    const double sza[4] = {tz, 0.0, tz - sz, -sz};
-    double acc = 0.0;
+template <typename S>
+__device__ __noinline__ S closed_nxy(S X, S Y, S Z, S tx, S ty, S tz, S sx, S sy, S sz) {
+    const S zero = s_const<S>(0.0);
+    const S sxa[4] = {tx, zero, tx - sx, -sx};
+    const S sya[4] = {zero, -sy, ty, ty - sy};
+    const S sza[4] = {tz, zero, tz - sz, -sz};
+    S acc = zero;
 #pragma unroll 1
     for (int a = 0; a < 4; ++a) {
-        double ya = 0.0;
+        S ya = zero;
 #pragma unroll 1
         for (int b = 0; b < 4; ++b) {
-            double zb = 0.0;
+            S zb = zero;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
-                const double v = newell_g(X + sxa[a], Y + sya[b], Z + sza[c]);
-                zb += (c == 0 || c == 3) ? v : -v;
+                const S v = newell_g<S>(X + sxa[a], Y + sya[b], Z + sza[c]);
+                if (c == 0 || c == 3) zb += v; else zb -= v;
             }
-            ya += (b == 0 || b == 3) ? zb : -zb;
+            if (b == 0 || b == 3) ya += zb; else ya -= zb;
         }
-        acc += (a == 0 || a == 3) ? ya : -ya;
+        if (a == 0 || a == 3) acc += ya; else acc -= ya;
     }
-    return acc / (4.0 * kPi * tx * ty * tz);
+    return acc / (4.0 * kPi * (tx * ty * tz));
 }
 
 // All six components: N_yy, N_zz from N_xx and N_xz, N_yz from N_xy by axis
 // permutation (Sec. 2).  out = {xx, yy, zz, xy, xz, yz}.
-__device__ void closed_tensor(double X, double Y, double Z, const double t[3], const double s[3],
-                              double out[6]) {
-    out[0] = closed_nxx(X, Y, Z, t[0], t[1], t[2], s[0], s[1], s[2]);
-    out[1] = closed_nxx(Y, X, Z, t[1], t[0], t[2], s[1], s[0], s[2]);
-    out[2] = closed_nxx(Z, Y, X, t[2], t[1], t[0], s[2], s[1], s[0]);
-    out[3] = closed_nxy(X, Y, Z, t[0], t[1], t[2], s[0], s[1], s[2]);
-    out[4] = closed_nxy(X, Z, Y, t[0], t[2], t[1], s[0], s[2], s[1]);
-    out[5] = closed_nxy(Z, Y, X, t[2], t[1], t[0], s[2], s[1], s[0]);
+template <typename S>
+__device__ void closed_tensor(S X, S Y, S Z, const S t[3], const S s[3], S out[6]) {
+    out[0] = closed_nxx<S>(X, Y, Z, t[0], t[1], t[2], s[0], s[1], s[2]);
+    out[1] = closed_nxx<S>(Y, X, Z, t[1], t[0], t[2], s[1], s[0], s[2]);
+    out[2] = closed_nxx<S>(Z, Y, X, t[2], t[1], t[0], s[2], s[1], s[0]);
+    out[3] = closed_nxy<S>(X, Y, Z, t[0], t[1], t[2], s[0], s[1], s[2]);
+    out[4] = closed_nxy<S>(X, Z, Y, t[0], t[2], t[1], s[0], s[2], s[1]);
+    out[5] = closed_nxy<S>(Z, Y, X, t[2], t[1], t[0], s[2], s[1], s[0]);
 }
 
 // ---- far field: composite Gauss-Legendre quadrature -----------------------
@@ -277,7 +316,7 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
     const double gap = sqrt(gap2);
     const double e = fmax(fmax(t[0], t[1]), fmax(s[0], s[1]));
     if (gap < e) {
-        closed_tensor(X, Y, Z, t, s, out);
+        closed_tensor<double>(X, Y, Z, t, s, out);
         return;
     }
     const double wcap = 0.5 * gap;
@@ -290,6 +329,140 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
             if (ws[p] > 0.0) widest = fmax(widest, ws[p] / ceil(ws[p] / wcap));
     }
     quadrature_tensor(X, Y, Z, t, s, far_nodes(gap / widest), wcap, out);
+}
+
+// ---- d/dt of the tensor ----------------------------------------------------
+//
+// Derivative of N(target <- source) along (dtz, dsz, dZ): target z-edge, source
+// z-edge and z-offset (the in-plane quantities are fixed).  Near pairs: the
+// closed form in Dual arithmetic.  Far pairs: differentiating the volume
+// integral itself.  With I(a, b, Z) = int dw T(w; a, b) Phi(Z + w), T the
+// z-difference density of edges a (target) and b (source) and Phi the in-plane
+// integral of the Hessian of 1/r,
+//   dI/da = int_{a-b}^{a} Phi,   dI/db = int_{-b}^{a-b} Phi,
+//   dI/dZ = int_{max(0,a-b)}^{a} Phi - int_{-b}^{min(0,a-b)} Phi
+// (dT/da, dT/db are indicators; dI/dZ by parts with dT/dw = +1, 0, -1 on the
+// three pieces), and N = -I / (4 pi |tau|) adds -N dtz / tz.
+
+// Plain composite Gauss-Legendre rule on [lo, hi], sub-pieces <= wcap.
+struct IntervalRule {
+    double lo, len;
+    int cuts, count;
+};
+
+__device__ void interval_rule(IntervalRule &r, double lo, double hi, double wcap, int n) {
+    r.lo = lo;
+    const double w = hi - lo;
+    r.cuts = w > 0.0 ? (int)ceil(w / wcap) : 0;
+    r.len = r.cuts > 0 ? w / r.cuts : 0.0;
+    r.count = r.cuts * n;
+}
+
+__device__ __forceinline__ void interval_node(const IntervalRule &r, int n, int k, double &u, double &W) {
+    const int c = k / n, i = k - c * n;
+    const double half = 0.5 * r.len;
+    u = r.lo + r.len * c + half + half * c_gl_x[n][i];
+    W = half * c_gl_w[n][i];
+}
+
+__device__ void quadrature_tensor_dt(double X, double Y, double Z, const double t[3],
+                                     const double s[3], int n, double wcap, double dtz, double dsz,
+                                     double dZ, double out[6], double dout[6]) {
+    AxisRule rx, ry, rz;
+    axis_rule(rx, t[0], s[0], wcap, n);
+    axis_rule(ry, t[1], s[1], wcap, n);
+    axis_rule(rz, t[2], s[2], wcap, n);
+    const double a = t[2], b = s[2];
+    // derivative intervals and their coefficients
+    IntervalRule ir[4];
+    double coef[4];
+    interval_rule(ir[0], a - b, a, wcap, n);
+    coef[0] = dtz;
+    interval_rule(ir[1], -b, a - b, wcap, n);
+    coef[1] = dsz;
+    interval_rule(ir[2], fmax(0.0, a - b), a, wcap, n);
+    coef[2] = dZ;
+    interval_rule(ir[3], -b, fmin(0.0, a - b), wcap, n);
+    coef[3] = -dZ;
+    double h[6] = {0, 0, 0, 0, 0, 0}, dh[6] = {0, 0, 0, 0, 0, 0};
+    for (int kx = 0; kx < rx.count; ++kx) {
+        double ux, wx;
+        axis_node(rx, n, kx, ux, wx);
+        const double dxv = X + ux;
+        for (int ky = 0; ky < ry.count; ++ky) {
+            double uy, wy;
+            axis_node(ry, n, ky, uy, wy);
+            const double dyv = Y + uy;
+            const double wxy = wx * wy;
+            // value: trapezoid-weighted nodes; derivative: interval nodes
+            for (int part = 0; part < 5; ++part) {
+                if (part > 0 && coef[part - 1] == 0.0) continue;
+                const int cnt = part == 0 ? rz.count : ir[part - 1].count;
+                for (int kz = 0; kz < cnt; ++kz) {
+                    double uz, wz;
+                    if (part == 0)
+                        axis_node(rz, n, kz, uz, wz);
+                    else {
+                        interval_node(ir[part - 1], n, kz, uz, wz);
+                        wz *= coef[part - 1];
+                    }
+                    const double dzv = Z + uz;
+                    const double r2 = dxv * dxv + dyv * dyv + dzv * dzv;
+                    const double ir1 = 1.0 / sqrt(r2);
+                    const double ir2 = ir1 * ir1;
+                    const double q = wxy * wz * ir1 * ir2 * ir2;
+                    const double q3 = 3.0 * q;
+                    double *acc = part == 0 ? h : dh;
+                    acc[0] += q3 * dxv * dxv - q * r2;
+                    acc[1] += q3 * dyv * dyv - q * r2;
+                    acc[2] += q3 * dzv * dzv - q * r2;
+                    acc[3] += q3 * dxv * dyv;
+                    acc[4] += q3 * dxv * dzv;
+                    acc[5] += q3 * dyv * dzv;
+                }
+            }
+        }
+    }
+    const double sc = -1.0 / (4.0 * kPi * t[0] * t[1] * t[2]);
+    for (int c = 0; c < 6; ++c) {
+        out[c] = h[c] * sc;
+        dout[c] = dh[c] * sc - out[c] * dtz / t[2];
+    }
+}
+
+// Value and derivative of the evaluation used everywhere (tensor_eval).
+__device__ void tensor_eval_dt(double X, double Y, double Z, const double t[3], const double s[3],
+                               double dtz, double dsz, double dZ, double out[6], double dout[6]) {
+    const double o[3] = {X, Y, Z};
+    double gap2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double lo = o[k] - s[k], hi = o[k] + t[k];
+        const double c = lo > 0.0 ? lo : (hi < 0.0 ? hi : 0.0);
+        gap2 += c * c;
+    }
+    const double gap = sqrt(gap2);
+    const double e = fmax(fmax(t[0], t[1]), fmax(s[0], s[1]));
+    if (gap < e) {
+        const Dual td[3] = {{t[0], 0.0}, {t[1], 0.0}, {t[2], dtz}};
+        const Dual sd[3] = {{s[0], 0.0}, {s[1], 0.0}, {s[2], dsz}};
+        Dual r[6];
+        closed_tensor<Dual>(Dual{X, 0.0}, Dual{Y, 0.0}, Dual{Z, dZ}, td, sd, r);
+        for (int c = 0; c < 6; ++c) {
+            out[c] = r[c].v;
+            dout[c] = r[c].d;
+        }
+        return;
+    }
+    const double wcap = 0.5 * gap;
+    double widest = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double br0 = -s[k], br1 = fmin(0.0, t[k] - s[k]), br2 = fmax(0.0, t[k] - s[k]),
+                     br3 = t[k];
+        const double ws[3] = {br1 - br0, br2 - br1, br3 - br2};
+        for (int p = 0; p < 3; ++p)
+            if (ws[p] > 0.0) widest = fmax(widest, ws[p] / ceil(ws[p] / wcap));
+    }
+    quadrature_tensor_dt(X, Y, Z, t, s, far_nodes(gap / widest), wcap, dtz, dsz, dZ, out, dout);
 }
 
 // ---- kernels ---------------------------------------------------------------
@@ -344,6 +517,75 @@ __global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
             base[(size_t)2 * Px * Py + o] = make_double2(sgx * N[4], sgy * N[5]);
         }
     }
+}
+
+// geom[n][12]: X, Y, Z, tx, ty, tz, sx, sy, sz, dtz, dsz, dZ -> out[n][6], dout[n][6]
+__global__ void k_tensor_points_dt(int n, const double *__restrict__ geom, double *__restrict__ out,
+                                   double *__restrict__ dout) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *g = geom + (size_t)i * 12;
+    const double t[3] = {g[3], g[4], g[5]}, s[3] = {g[6], g[7], g[8]};
+    double r[6], dr[6];
+    tensor_eval_dt(g[0], g[1], g[2], t, s, g[9], g[10], g[11], r, dr);
+    for (int c = 0; c < 6; ++c) {
+        out[(size_t)i * 6 + c] = r[c];
+        dout[(size_t)i * 6 + c] = dr[c];
+    }
+}
+
+cudaError_t launch_tensor_points_dt(int n, const double *geom, double *out, double *dout,
+                                    cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_tensor_points_dt<<<(n + 127) / 128, 128, 0, st>>>(n, geom, out, dout);
+    return cudaGetLastError();
+}
+
+// d N(i <- j) / d t_layer for all L*L pairs (P = i*L + j) of [p0, p0 + np),
+// written with the in-plane parity like k_kernel_planes.  Seeds: the target
+// edge moves if i == layer, the source edge if j == layer, and the offset
+// z_i - z_j by [i > layer] - [j > layer].
+__global__ void k_dkernel_planes(double2 *__restrict__ planes, int p0, int np, int L, int layer,
+                                 int nx, int ny, double dx, double dy, int log2Px, int log2Py,
+                                 const double *__restrict__ z, const double *__restrict__ th) {
+    const long long total = (long long)np * nx * ny;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int p = (int)(idx % nx);
+    const int q = (int)((idx / nx) % ny);
+    const int P = (int)(idx / ((long long)nx * ny));
+    const int i = (p0 + P) / L, j = (p0 + P) % L;
+    const double dtz = i == layer ? 1.0 : 0.0, dsz = j == layer ? 1.0 : 0.0;
+    const double dZ = (i > layer ? 1.0 : 0.0) - (j > layer ? 1.0 : 0.0);
+    if (dtz == 0.0 && dsz == 0.0 && dZ == 0.0) return;  // planes are zeroed beforehand
+    const double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
+    double N[6], dN[6];
+    tensor_eval_dt(p * dx, q * dy, z[i] - z[j], t, s, dtz, dsz, dZ, N, dN);
+    const int Px = 1 << log2Px, Py = 1 << log2Py;
+    double2 *base = planes + (size_t)P * 3 * Px * Py;
+    for (int my = 0; my < 2; ++my) {
+        if (my && q == 0) continue;
+        const int yi = my ? Py - q : q;
+        const double sgy = my ? -1.0 : 1.0;
+        for (int mx = 0; mx < 2; ++mx) {
+            if (mx && p == 0) continue;
+            const int xi = mx ? Px - p : p;
+            const double sgx = mx ? -1.0 : 1.0;
+            const size_t o = (size_t)yi * Px + xi;
+            base[o] = make_double2(dN[0], dN[1]);
+            base[(size_t)Px * Py + o] = make_double2(dN[2], sgx * sgy * dN[3]);
+            base[(size_t)2 * Px * Py + o] = make_double2(sgx * dN[4], sgy * dN[5]);
+        }
+    }
+}
+
+cudaError_t launch_dkernel_planes(double2 *planes, int p0, int np, int L, int layer, int nx, int ny,
+                                  double dx, double dy, int log2Px, int log2Py, const double *z,
+                                  const double *th, cudaStream_t st) {
+    const long long total = (long long)np * nx * ny;
+    k_dkernel_planes<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(planes, p0, np, L, layer, nx, ny, dx,
+                                                                      dy, log2Px, log2Py, z, th);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pair_i,
@@ -424,42 +666,44 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
     return cudaGetLastError();
 }
 
-// Quadrant kx <= Px/2, ky <= Py/2 of the transformed planes -> plan tensor.
+// Quadrant kx <= Px/2, ky <= Py/2 of the transformed planes -> plan tensor,
+// stored entry u holding ky = u_kyq(u) (layout.cuh).
 // plane 0 = FFT(N_xx) + i FFT(N_yy), both real; plane 1 = FFT(N_zz) + i FFT(N_xy),
 // both real; plane 2 = FFT(N_xz) + i FFT(N_yz) = i a - b with FFT(N_xz) = i a,
 // FFT(N_yz) = i b.
 template <typename T>
 __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, int npairs,
-                          int log2Px, int log2Py, T *__restrict__ tensor) {
+                          int log2Px, int log2Py, int QyS, T *__restrict__ tensor) {
     const int Px = 1 << log2Px, Py = 1 << log2Py;
     const int Kx = Px / 2 + 1, Qy = Py / 2 + 1;
     const long long total = (long long)np * Kx * Qy;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int kq = (int)(idx % Qy);
+    const int u = (int)(idx % Qy);
     const int kx = (int)((idx / Qy) % Kx);
     const int P = (int)(idx / ((long long)Qy * Kx));
+    const int kq = u_kyq(u, log2Py);
     const double2 *base = planes + (size_t)P * 3 * Px * Py + (size_t)kq * Px + kx;
     const double2 A = base[0], Bp = base[(size_t)Px * Py], C = base[(size_t)2 * Px * Py];
     const double sc = 1.0 / ((double)Px * (double)Py);
-    T *o = tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * Qy + kq;
-    o[0 * Qy] = (T)(A.x * sc);
-    o[1 * Qy] = (T)(A.y * sc);
-    o[2 * Qy] = (T)(Bp.x * sc);
-    o[3 * Qy] = (T)(Bp.y * sc);
-    o[4 * Qy] = (T)(C.y * sc);
-    o[5 * Qy] = (T)(-C.x * sc);
+    T *o = tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * QyS + u;
+    o[0 * QyS] = (T)(A.x * sc);
+    o[1 * QyS] = (T)(A.y * sc);
+    o[2 * QyS] = (T)(Bp.x * sc);
+    o[3 * QyS] = (T)(Bp.y * sc);
+    o[4 * QyS] = (T)(C.y * sc);
+    o[5 * QyS] = (T)(-C.x * sc);
 }
 
 cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs, int log2Px,
-                                  int log2Py, void *tensor, bool fp64, cudaStream_t st) {
+                                  int log2Py, int QyS, void *tensor, bool fp64, cudaStream_t st) {
     const long long total = (long long)np * ((1 << log2Px) / 2 + 1) * ((1 << log2Py) / 2 + 1);
     const unsigned grid = (unsigned)((total + 255) / 256);
     if (fp64)
-        k_extract<double><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py,
+        k_extract<double><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
                                                 (double *)tensor);
     else
-        k_extract<float><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py,
+        k_extract<float><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
                                                (float *)tensor);
     return cudaGetLastError();
 }

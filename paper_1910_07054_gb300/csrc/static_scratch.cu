@@ -16,10 +16,12 @@
 // nothing needs clearing, but two calls whose GPU work overlaps (different
 // streams, or different host threads) race on it.
 #include <cmath>
+#include <cstdint>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+#include "layout.cuh"
 
 namespace demag {
 
@@ -59,7 +61,7 @@ static void host_twiddles(int log2n, std::vector<C> &tw) {
     }
 }
 
-static int log2_ceil(int v) {
+static int log2_ceil_min4(int v) {
     int l = 0;
     while ((1 << l) < v) ++l;
     return l < 2 ? 2 : l;
@@ -74,6 +76,8 @@ extern "C" demag_status demag_apply_static(const void *tensor, const double *thi
                                            void *H, int B, void *stream) {
     if (!tensor || !thickness || !m || !H) return fail(DEMAG_EINVAL, "a pointer argument is NULL");
     if (m == H) return fail(DEMAG_EINVAL, "H must not alias m");
+    if (reinterpret_cast<uintptr_t>(tensor) % 16 != 0)
+        return fail(DEMAG_EINVAL, "tensor must be 16-byte aligned");
     if (nx < 1 || ny < 1 || L < 1 || B < 1) return fail(DEMAG_EINVAL, "nx, ny, L and B must be >= 1");
     if (nx > 2048 || ny > 2048 || L > 256) return fail(DEMAG_EUNSUPPORTED, "size above the library limits");
     if (precision != DEMAG_PREC_FP64 && precision != DEMAG_PREC_FP32)
@@ -84,7 +88,7 @@ extern "C" demag_status demag_apply_static(const void *tensor, const double *thi
             return fail(DEMAG_EINVAL, "thickness[" + std::to_string(l) + "] must be finite and > 0");
     if ((long long)B * L * 3 > 65535) return fail(DEMAG_EUNSUPPORTED, "B * L * 3 must be <= 65535");
     const bool fp64 = precision == DEMAG_PREC_FP64;
-    const int log2Px = log2_ceil(2 * nx), log2Py = log2_ceil(2 * ny);
+    const int log2Px = log2_ceil_min4(2 * nx), log2Py = log2_ceil_min4(2 * ny);
     if (L > fused_max_layers(fp64, log2Py))
         return fail(DEMAG_EUNSUPPORTED, "layer count above the fused contraction limit for this grid");
     const size_t real = fp64 ? 8 : 4, cpx = 2 * real;
@@ -133,6 +137,7 @@ extern "C" demag_status demag_apply_static(const void *tensor, const double *thi
     a.log2Px = log2Px;
     a.log2Py = log2Py;
     a.npairs = L * (L + 1) / 2;
+    a.QyS = tensor_row(log2Py, fp64);
     a.tensor = tensor;
     a.ratio = b + spec + twx + twy;
     a.twx = b + spec;

@@ -84,19 +84,40 @@ def test_tensor_points_match_oracle():
     assert np.allclose(N[len(g) - 5, :3], 1.0 / 3.0, atol=1e-15)
 
 
-@pytest.mark.parametrize("nx,ny,th", [(7, 5, (1.0, 0.5, 2.0)), (4, 9, (0.8,)), (12, 3, (0.6, 3.0))])
+def _stored_ky(Py):
+    """y-frequency held by each stored entry u (the documented order of
+    demag_plan_tensor: bit-reversed positions, one partner of each mirror pair)."""
+    n = Py.bit_length() - 1
+    out = []
+    for u in range(Py // 2 + 1):
+        if u < 2:
+            p1 = u
+        else:
+            m = (u - 1).bit_length()
+            p1 = (1 << m) + u - (1 << (m - 1)) - 1
+        k = int(format(p1, "0%db" % n)[::-1], 2)
+        out.append(min(k, Py - k))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("nx,ny,th", [(7, 5, (1.0, 0.5, 2.0)), (4, 9, (0.8,)), (12, 3, (0.6, 3.0)),
+                                      (16, 16, (1.0, 2.0))])
 def test_plan_tensor_matches_oracle_spectrum(nx, ny, th):
     """The stored Fourier tensor equals the oracle's kernels placed on the same
-    padded grid and transformed by numpy's FFT (quadrant, divided by Px Py)."""
+    padded grid and transformed by numpy's FFT (quadrant, divided by Px Py),
+    in the documented storage order."""
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP64)
     info = plan.info
-    Px, Py, L, npairs = info["Px"], info["Py"], info["L"], info["npairs"]
+    Px, Py, L, npairs, QyS = info["Px"], info["Py"], info["L"], info["npairs"], info["QyS"]
     Kx, Qy = Px // 2 + 1, Py // 2 + 1
-    out = torch.empty(Kx * npairs * 6 * Qy, dtype=torch.float64, device="cuda")
+    out = torch.empty(Kx * npairs * 6 * QyS, dtype=torch.float64, device="cuda")
     dm.demag_plan_tensor(plan.handle, out)
     torch.cuda.synchronize()
-    T = out.cpu().numpy().reshape(Kx, npairs, 6, Qy)
+    T = out.cpu().numpy().reshape(Kx, npairs, 6, QyS)
     plan.close()
+    assert np.all(T[..., Qy:] == 0.0)
+    ky_of_u = _stored_ky(Py)
+    assert sorted(ky_of_u.tolist()) == list(range(Qy))
     K = reading_kernels(nx, ny, 2.0, 2.0, tuple(th))
     pairs = [(i, j) for i in range(L) for j in range(i, L)]
     qs = np.arange(-(ny - 1), ny) % Py
@@ -108,10 +129,10 @@ def test_plan_tensor_matches_oracle_spectrum(nx, ny, th):
         ref = np.stack([S[0].real, S[1].real, S[2].real, S[3].real, S[4].imag, S[5].imag])
         # the structure: even components have real spectra, odd ones imaginary
         assert np.abs(S[:4].imag).max() < 1e-14 and np.abs(S[4:].real).max() < 1e-14
-        ref_q = ref[:, :Qy, :Kx]                     # [component, ky, kx]
-        got_q = np.transpose(T[:, P], (1, 2, 0))     # [kx, component, ky] -> same order
-        sc = np.abs(ref_q).max()
-        assert np.abs(got_q - ref_q).max() < 1e-12 * sc
+        ref_u = ref[:, ky_of_u, :Kx]                  # [component, u, kx]
+        got_u = np.transpose(T[:, P, :, :Qy], (1, 2, 0))
+        sc = np.abs(ref_u).max()
+        assert np.abs(got_u - ref_u).max() < 1e-12 * sc
 
 
 def test_plain32_fp64_matches_direct_sum():

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 def _stored_tensor(plan):
     info = plan.info
-    n = (info["Px"] // 2 + 1) * info["npairs"] * 6 * (info["Py"] // 2 + 1)
+    n = (info["Px"] // 2 + 1) * info["npairs"] * 6 * info["QyS"]
     T = torch.empty(n, dtype=plan.dtype, device="cuda")
     dm.demag_plan_tensor(plan.handle, T)
     return T
