@@ -53,8 +53,12 @@ typedef enum {
 } demag_status;
 
 typedef enum {
-    DEMAG_PREC_FP64 = 0,     /* FFTs and layer contraction in double          */
-    DEMAG_PREC_FP32 = 1      /* FFTs and layer contraction in float           */
+    DEMAG_PREC_FP64 = 0,       /* FFTs and layer contraction in double          */
+    DEMAG_PREC_FP32 = 1,       /* FFTs and layer contraction in float           */
+    DEMAG_PREC_SPLIT_TF32 = 2  /* float FFTs; the contraction as dense products
+                                  on the tensor cores in three TF32 passes
+                                  (a_hi b_hi + a_hi b_lo + a_lo b_hi, float
+                                  accumulation), for batches of states        */
 } demag_precision;
 
 typedef struct demag_plan *demag_plan_t;
@@ -81,7 +85,10 @@ const char *demag_last_error(void);
  *   dx, dy     in-plane cell edges, > 0 and finite
  *   thickness  HOST array of L layer thicknesses, each > 0 and finite
  *   L          number of layers, 1 <= L <= 256
- *   precision  a demag_precision value
+ *   precision  a demag_precision value; DEMAG_PREC_SPLIT_TF32 needs
+ *              (6 L^2 + 12 L B + 12 L B) floats (L padded to 16, B to 8)
+ *              within 220 KB of shared memory, and its tensor is stored in
+ *              the layout [kx][u][pair][component] (see demag_plan_tensor)
  *   max_batch  largest batch B later passed to demag_apply, >= 1
  *   stream     stream for the set-up work; the call synchronises this stream
  *              before it returns
@@ -121,7 +128,12 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
  *   path 2: column FFT, contraction and inverse column FFT as three kernels
  *           through a [Kx][Py][B][L][3] complex workspace (allocated here on
  *           first use).
- *   path 0: the default choice of demag_plan_create (1 when it fits, else 2).
+ *   path 3: (DEMAG_PREC_SPLIT_TF32 plans) column kernels of path 2 with the
+ *           contraction as dense L x L by L x B products on the FP32 cores.
+ *   path 4: (DEMAG_PREC_SPLIT_TF32 plans, their default) the same products
+ *           on the tensor cores in three TF32 passes.
+ *   path 0: the default choice of demag_plan_create (1 when it fits, else 2;
+ *           4 for DEMAG_PREC_SPLIT_TF32).
  * Both paths compute the same field (Eq. FFT_v2); this entry point exists to
  * test and time them against each other.  Errors: DEMAG_EINVAL, DEMAG_ENOMEM,
  * DEMAG_EUNSUPPORTED (the path cannot hold this plan).
@@ -219,7 +231,10 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
  * demag_plan_tensor - copy of the stored Fourier-space tensor.
  *
  * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,
- * layout [kx][pair][component][u] with pair (i <= j) numbered row by row
+ * layout [kx][pair][component][u] (DEMAG_PREC_SPLIT_TF32 plans:
+ * (Px/2+1) * (Py/2+1) * NB floats, layout [kx][u][pair][component] with
+ * NB = npairs * 6 rounded up to a multiple of 4, the padding zero)
+ * with pair (i <= j) numbered row by row
  * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components
  * {Re N_xx, Re N_yy, Re N_zz, Re N_xy, Im N_xz, Im N_yz} of the 2D DFT of
  * N(i <- j) on the padded grid, divided by Px*Py.  Entry u < Py/2 + 1 holds

@@ -136,3 +136,31 @@ def fft3d(Kz, m, Ms):
     H = np.fft.ifftn(Hhat, axes=(-3, -2, -1)).real[:, :, :L, :ny, :nx] * (-Ms)
     H = np.moveaxis(H, 2, 1)
     return H if batched else H[0]
+
+
+def hybrid_targets(pair_kernel, m, Ms, targets):
+    """Eq. FFT_v2 for selected target layers only, one layer pair at a time
+    (bounded memory for large stacks): H_i for i in targets.
+
+    pair_kernel(i, j) -> [6, 2ny-1, 2nx-1] kernel of the pair; m: [L, 3, ny, nx].
+    Returns {i: H_i [3, ny, nx]}.
+    """
+    m = np.asarray(m, dtype=np.float64)
+    L, _, ny, nx = m.shape
+    mp = np.zeros((L, 3, 2 * ny, 2 * nx))
+    mp[..., :ny, :nx] = m
+    mhat = np.fft.fft2(mp, axes=(-2, -1))
+    qs = np.arange(-(ny - 1), ny) % (2 * ny)
+    ps = np.arange(-(nx - 1), nx) % (2 * nx)
+    out = {}
+    for i in targets:
+        Hhat = np.zeros((3, 2 * ny, 2 * nx), dtype=complex)
+        for j in range(L):
+            Kp = np.zeros((6, 2 * ny, 2 * nx))
+            Kp[:, qs[:, None], ps[None, :]] = pair_kernel(i, j)
+            Khat = np.fft.fft2(Kp, axes=(-2, -1))
+            for a in range(3):
+                for b in range(3):
+                    Hhat[a] += Khat[_COMP[a][b]] * mhat[j, b]
+        out[i] = np.fft.ifft2(Hhat, axes=(-2, -1)).real[..., :ny, :nx] * (-Ms)
+    return out

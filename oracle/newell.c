@@ -251,6 +251,26 @@ void oracle_tensor(int mode, double X, double Y, double Z, const double *t, cons
     reading_tensor(X, Y, Z, t, s, out);
 }
 
+/* One layer pair of oracle_layer_kernels (full offsets): K[6][2ny-1][2nx-1]
+ * for target layer i, source layer j. */
+void oracle_pair_kernel(int mode, int nx, int ny, double dx, double dy, int L, const double *th, int i,
+                        int j, double *K)
+{
+    double zi = 0.0, zj = 0.0;
+    for (int l = 0; l < i; ++l) zi += th[l];
+    for (int l = 0; l < j; ++l) zj += th[l];
+    int PW = 2 * nx - 1, QH = 2 * ny - 1;
+    long long total = (long long)QH * PW;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long e = 0; e < total; ++e) {
+        int pi = (int)(e % PW), qi = (int)(e / PW);
+        double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
+        double out[6];
+        oracle_tensor(mode, (pi - (nx - 1)) * dx, (qi - (ny - 1)) * dy, zi - zj, t, s, 0, out, NULL);
+        for (int c = 0; c < 6; ++c) K[((size_t)c * QH + qi) * PW + pi] = out[c];
+    }
+}
+
 /* Derivative of N(target <- source) along (dtz, dsz, dZ) (target z-edge,
  * source z-edge, z-offset), by a central difference of the exact _Float128
  * formula with step h: truncation O(h^2), rounding ~1e-34 / h. */

@@ -38,6 +38,9 @@ def lib():
         L.oracle_layer_kernels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, dp]
         L.oracle_layer_kernels.restype = None
+        L.oracle_pair_kernel.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp]
+        L.oracle_pair_kernel.restype = None
         L.oracle_tensor_dt.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, dp]
@@ -130,4 +133,14 @@ def layer_dkernels(nx, ny, dx, dy, thickness, layer, h=1e-9):
     K = np.zeros((L, L, 6, 2 * ny - 1, 2 * nx - 1))
     lib().oracle_layer_dkernels(int(nx), int(ny), float(dx), float(dy), int(L), _dp(th), int(layer),
                                 float(h), _dp(K))
+    return K
+
+
+def pair_kernel(nx, ny, dx, dy, thickness, i, j, mode=READING_D):
+    """Kernel of one layer pair (target i, source j) at every in-plane offset:
+    [6, 2ny-1, 2nx-1], offset index + n - 1 (as layer_kernels(full=True)[i, j])."""
+    th = np.ascontiguousarray(thickness, dtype=np.float64)
+    K = np.zeros((6, 2 * ny - 1, 2 * nx - 1))
+    lib().oracle_pair_kernel(int(mode), int(nx), int(ny), float(dx), float(dy), int(th.size), _dp(th),
+                             int(i), int(j), _dp(K))
     return K

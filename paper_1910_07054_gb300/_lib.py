@@ -12,7 +12,7 @@ import os
 from . import build as _build
 
 DEMAG_OK, DEMAG_EINVAL, DEMAG_ENOMEM, DEMAG_ECUDA, DEMAG_EUNSUPPORTED = range(5)
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_SPLIT_TF32 = 0, 1, 2
 
 _lib = None
 
@@ -119,7 +119,7 @@ def demag_plan_info(plan):
 
 def _field_check(t, info, name, device=True):
     import torch
-    want = torch.float64 if info["precision"] == PREC_FP64 else torch.float32
+    want = torch.float64 if info["precision"] == PREC_FP64 else torch.float32  # split-TF32: float
     if t.dtype != want:
         raise TypeError("%s must be %s for this plan, got %s" % (name, want, t.dtype))
     if not t.is_contiguous():

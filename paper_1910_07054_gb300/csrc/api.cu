@@ -159,7 +159,8 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
                 break;
             }
             if ((e = launch_extract_tensor(planes, p0, np, npairs, p->log2Px, p->log2Py, p->QyS,
-                                           dst, p->precision == DEMAG_PREC_FP64, st)) !=
+                                           dst, p->precision == DEMAG_PREC_FP64, st,
+                                           layer < 0 ? p->umajor : 0)) !=
                 cudaSuccess) {
                 rc = cuda_fail(e, "tensor extraction kernel");
                 break;
@@ -237,7 +238,8 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     for (int l = 0; l < L; ++l)
         if (!(std::isfinite(thickness[l]) && thickness[l] > 0))
             return fail(DEMAG_EINVAL, "thickness[" + std::to_string(l) + "] must be finite and > 0");
-    if (precision != DEMAG_PREC_FP64 && precision != DEMAG_PREC_FP32)
+    if (precision != DEMAG_PREC_FP64 && precision != DEMAG_PREC_FP32 &&
+        precision != DEMAG_PREC_SPLIT_TF32)
         return fail(DEMAG_EINVAL, "unknown precision");
     if (max_batch < 1) return fail(DEMAG_EINVAL, "max_batch must be >= 1");
     if ((long long)max_batch * L * 3 > 65535)
@@ -262,10 +264,21 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     p->QyS = tensor_row(p->log2Py, precision == DEMAG_PREC_FP64);
     p->npairs = L * (L + 1) / 2;
     const bool fp64 = precision == DEMAG_PREC_FP64;
-    p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
-    if (p->split && !split_supported(L, max_batch, fp64)) {
-        delete p;
-        return fail(DEMAG_EUNSUPPORTED, "layer count x batch above the contraction kernels' limits");
+    if (precision == DEMAG_PREC_SPLIT_TF32) {
+        // split path, dense-product contraction on the tensor cores
+        if (!gemm_supported(L, max_batch)) {
+            delete p;
+            return fail(DEMAG_EUNSUPPORTED, "layer count x batch above the dense-product contraction limit");
+        }
+        p->split = 1;
+        p->umajor = 1;
+        p->contract_mode = 2;
+    } else {
+        p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
+        if (p->split && !split_supported(L, max_batch, fp64)) {
+            delete p;
+            return fail(DEMAG_EUNSUPPORTED, "layer count x batch above the contraction kernels' limits");
+        }
     }
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&p->device);
@@ -276,7 +289,8 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     demag_status rc = upload_gauss_legendre();
     const size_t real = fp64 ? sizeof(double) : sizeof(float);
     const size_t cpx = 2 * real;
-    p->tensor_bytes = (size_t)p->Kx * p->npairs * 6 * p->QyS * real;
+    p->tensor_bytes = p->umajor ? (size_t)p->Kx * p->Qy * umajor_block(p->npairs) * real
+                                : (size_t)p->Kx * p->npairs * 6 * p->QyS * real;
     p->field_bytes_per_state = (size_t)L * 3 * ny * nx * real;
     if (rc == DEMAG_OK) rc = dalloc(&p->d_tensor, p->tensor_bytes, "tensor");
     if (rc == DEMAG_OK && (e = cudaMemset(p->d_tensor, 0, p->tensor_bytes)) != cudaSuccess)
@@ -357,6 +371,7 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.spec = plan->d_spec;
     a.spec2 = plan->d_spec2;
     a.split = plan->split;
+    a.contract_mode = plan->contract_mode;
     a.Ms = Ms;
     return a;
 }
@@ -414,6 +429,15 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
 demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
     const bool fp64 = plan->precision == DEMAG_PREC_FP64;
+    if (plan->umajor) {
+        if (path == 0) path = 4;
+        if (path != 3 && path != 4)
+            return fail(DEMAG_EUNSUPPORTED, "split-TF32 plans run path 3 or 4");
+        plan->contract_mode = path == 4 ? 2 : 1;
+        return DEMAG_OK;
+    }
+    if (path == 3 || path == 4)
+        return fail(DEMAG_EUNSUPPORTED, "paths 3 and 4 need a DEMAG_PREC_SPLIT_TF32 plan");
     if (path == 0) path = plan->L > fused_max_layers(fp64, plan->log2Py) ? 2 : 1;
     if (path == 1) {
         if (plan->L > fused_max_layers(fp64, plan->log2Py))
@@ -450,6 +474,8 @@ demag_status demag_apply_dthickness(demag_plan_t plan, const void *m, double Ms,
     demag_status rc = check_apply(plan, m, Ms, dH, B);
     if (rc != DEMAG_OK) return rc;
     if (layer < 0 || layer >= plan->L) return fail(DEMAG_EINVAL, "layer out of range");
+    if (plan->umajor)
+        return fail(DEMAG_EUNSUPPORTED, "thickness derivatives need a DEMAG_PREC_FP64 or DEMAG_PREC_FP32 plan");
     cudaStream_t st = (cudaStream_t)stream;
     DEMAG_TRY(ensure_dtensor(plan, layer, st));
     ApplyArgs a = apply_args(plan, Ms, B);
@@ -504,7 +530,7 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     out[6] = plan->max_batch;
     out[7] = plan->npairs;
     out[8] = plan->QyS;
-    out[9] = plan->split ? 2 : 1;
+    out[9] = plan->umajor ? (plan->contract_mode == 2 ? 4 : 3) : (plan->split ? 2 : 1);
     return DEMAG_OK;
 }
 

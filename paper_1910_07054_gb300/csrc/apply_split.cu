@@ -256,8 +256,8 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
     const int Py = 1 << a.log2Py;
     const int Kx = (1 << a.log2Px) / 2 + 1;
     const int planes = a.B * 3 * a.L;
-    int G = 16;
-    while (G > 1 && (size_t)G * (Py + 1) * sizeof(C) > 96 * 1024) G /= 2;
+    int G = 16;  // planes per column block: at most ~72 KB, so that 3 blocks share an SM
+    while (G > 1 && (size_t)G * (Py + 1) * sizeof(C) > 72 * 1024) G /= 2;
     if (G > planes) G = planes;
     const size_t smem_col = (size_t)G * (Py + 1) * sizeof(C);
     cudaError_t e;
@@ -272,6 +272,13 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
                                                                 Kx, planes, G, a.log2Py,
                                                                 (const C *)a.twy, a.log2twy);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.contract_mode != 0) {
+        if ((e = launch_contract_gemm(a, a.contract_mode == 2, st)) != cudaSuccess) return e;
+        k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec,
+                                                                    a.ny, Kx, planes, G, a.log2Py,
+                                                                    (const C *)a.twy, a.log2twy);
+        return cudaGetLastError();
+    }
     const int TU = split_tile<T>(a.L, a.B, 200 * 1024);
     const size_t smem_ct = (size_t)TU * 2 * planes * sizeof(C);
     if ((e = cudaFuncSetAttribute(k_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,0 +1,308 @@
+// Layer contraction as small dense matrix products, for batches of states.
+//
+// At one frequency k the contraction of Eq. FFT_v2, H(b, i) = sum_j N_k(i <- j)
+// m(b, j), with the symmetric blocks N = [[xx, xy, i xz], [xy, yy, i yz],
+// [i xz, i yz, zz]] (xx, yy, zz, xy real, xz, yz imaginary coefficients) splits
+// into 18 real products of L x L component matrices with L x B state matrices:
+//   Hr_x = Kxx Mr_x + s Kxy Mr_y -   Kxz Mi_z     Hi_x = Kxx Mi_x + s Kxy Mi_y +   Kxz Mr_z
+//   Hr_y = s Kxy Mr_x + Kyy Mr_y - s Kyz Mi_z     Hi_y = s Kxy Mi_x + Kyy Mi_y + s Kyz Mr_z
+//   Hr_z = -Kxz Mi_x - s Kyz Mi_y + Kzz Mr_z      Hi_z = Kxz Mr_x + s Kyz Mr_y + Kzz Mi_z
+// (s = -1 at the mirrored frequency Py - ky, where xy and yz change sign):
+// exactly 36 L^2 B flops, nothing spent on zero blocks.
+//
+// One block per (kx, stored entry u): the compact tensor of the entry (pairs
+// i <= j, [kx][u][pair][6], contiguous) is expanded into the six dense L x L
+// matrices in shared memory (the lower triangle from reciprocity, t_i N(i<-j)
+// = t_j N(j<-i)(-d)); the states at the entry's two positions are staged as
+// 12 L x B matrices; the products run either on the tensor cores in three
+// TF32 passes (a = a_hi + a_lo, b = b_hi + b_lo: a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, FP32 accumulation) or on the FP32 CUDA cores with the same data
+// movement; the result is written back in place.
+#include <cstdint>
+
+#include "fft.cuh"
+#include "internal.h"
+#include "layout.cuh"
+
+namespace demag {
+
+constexpr int kGemmThreads = 256;
+
+// Shared-memory row stride of the L x L and B x L operands: rows of 4 banks
+// apart, so the 8 x 4 lane pattern of an m16n8k8 fragment hits 32 banks.
+__host__ __device__ inline int gemm_stride(int Lp) { return Lp + 4; }
+
+// Padded sizes: L to a multiple of 16 (MMA rows), B to a multiple of 8 (MMA columns).
+__host__ __device__ inline int pad16(int v) { return (v + 15) / 16 * 16; }
+__host__ __device__ inline int pad8(int v) { return (v + 7) / 8 * 8; }
+
+// Operands (6 L x L matrices, 2 x 6 B x L matrices) and the output area
+// (2 positions x 6 matrices x L x B).
+size_t gemm_smem_bytes(int L, int B) {
+    const int Lp = pad16(L), Bp = pad8(B), S = gemm_stride(Lp);
+    return (size_t)(6 * Lp * S + 2 * 6 * Bp * S + 2 * 6 * Lp * Bp) * sizeof(float);
+}
+
+// The tensor-core variant keeps 2 x 8 accumulator tiles per warp: B <= 64.
+bool gemm_supported(int L, int B) { return pad8(B) <= 64 && gemm_smem_bytes(L, B) <= 220 * 1024; }
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Terms of the six output matrices: (component matrix, state matrix, sign
+// flag).  Component 0..5 = xx, yy, zz, xy, xz, yz.  State matrix 0..5 =
+// Mr_x, Mr_y, Mr_z, Mi_x, Mi_y, Mi_z.  Sign: +1 / -1, and "mirror" terms
+// (xy, yz) are further multiplied by s.
+struct Term {
+    int comp, state;
+    float sign;
+};
+__constant__ Term c_terms[6][3] = {
+    {{0, 0, 1.f}, {3, 1, 1.f}, {4, 5, -1.f}},   // Hr_x
+    {{0, 3, 1.f}, {3, 4, 1.f}, {4, 2, 1.f}},    // Hi_x
+    {{3, 0, 1.f}, {1, 1, 1.f}, {5, 5, -1.f}},   // Hr_y
+    {{3, 3, 1.f}, {1, 4, 1.f}, {5, 2, 1.f}},    // Hi_y
+    {{4, 3, -1.f}, {5, 4, -1.f}, {2, 2, 1.f}},  // Hr_z
+    {{4, 0, 1.f}, {5, 1, 1.f}, {2, 5, 1.f}},    // Hi_z
+};
+
+template <bool TC>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
+    float2 *__restrict__ spec2, const float *__restrict__ tensor_um, const float *__restrict__ ratio,
+    int L, int B, int log2Py, int npairs) {
+    extern __shared__ __align__(16) float smem_f[];
+    const int Lp = pad16(L), Bp = pad8(B), S = gemm_stride(Lp);
+    float *Kd = smem_f;                  // [6][Lp][S]: K_c[i][j]
+    float *Ms = smem_f + 6 * Lp * S;     // [2 positions][6][Bp][S]: M_s[b][j]
+    const int Py = 1 << log2Py, Qy = Py / 2 + 1;
+    const int planes = B * 3 * L;
+    const int kx = blockIdx.x, u = blockIdx.y;
+    int p1, p2;
+    u_positions(u, log2Py, p1, p2);
+    const int ky1 = bit_reverse(p1, log2Py);
+    const float s_pos[2] = {ky1 > Py / 2 ? -1.f : 1.f, ky1 > Py / 2 ? 1.f : -1.f};
+    const int npos = p2 != p1 ? 2 : 1;
+
+    // zero the operands (padding rows and columns stay zero), then expand the
+    // compact tensor
+    for (int e = threadIdx.x; e < 6 * Lp * S + 2 * 6 * Bp * S; e += kGemmThreads) smem_f[e] = 0.f;
+    __syncthreads();
+    // compact tensor of the entry: npairs * 6 floats, contiguous and 16-byte
+    // aligned; all loads of a thread are issued before any is used
+    const int NB = umajor_block(npairs);
+    const float4 *tu4 = reinterpret_cast<const float4 *>(tensor_um + ((size_t)kx * Qy + u) * NB);
+    const int n4 = NB / 4;
+    constexpr int kBatch = 8;
+    for (int base = threadIdx.x; base < n4; base += kGemmThreads * kBatch) {
+        float4 v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int e4 = base + k * kGemmThreads;
+            v[k] = e4 < n4 ? tu4[e4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int e4 = base + k * kGemmThreads;
+            if (e4 >= n4) break;
+            const float vals[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int e = 4 * e4 + w;
+                if (e >= npairs * 6) break;  // block padding
+                const int P = e / 6, c = e - P * 6;
+                // pair P = (a, b), a <= b, numbered row by row: invert the
+                // triangular count from the end, r = T - 1 - P
+                const int T = L * (L + 1) / 2, r = T - 1 - P;
+                int kk = (int)((sqrtf(8.f * (float)r + 1.f) - 1.f) * 0.5f);
+                while ((kk + 1) * (kk + 2) / 2 <= r) ++kk;
+                while (kk * (kk + 1) / 2 > r) --kk;
+                const int a = L - 1 - kk;
+                const int b = L - 1 - (r - kk * (kk + 1) / 2);
+                Kd[(c * Lp + a) * S + b] = vals[w];  // target a <- source b
+                if (b != a) {
+                    const float rr = ratio[b * L + a] * (c >= 4 ? -1.f : 1.f);  // target b <- source a
+                    Kd[(c * Lp + b) * S + a] = rr * vals[w];
+                }
+            }
+        }
+    }
+    // stage the states at the entry's positions: M[b][j] per (component, re/im)
+    float2 *sk = spec2 + (size_t)kx * Py * planes;
+    for (int pos = 0; pos < npos; ++pos) {
+        const float2 *row = sk + (size_t)(pos ? p2 : p1) * planes;
+        float *m = Ms + (size_t)pos * 6 * Bp * S;
+        for (int base = threadIdx.x; base < planes; base += kGemmThreads * kBatch) {
+            float2 v[kBatch];
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k) {
+                const int g = base + k * kGemmThreads;
+                v[k] = g < planes ? row[g] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k) {
+                const int g = base + k * kGemmThreads;
+                if (g >= planes) break;
+                const int b = g / (3 * L), rem = g - b * 3 * L, j = rem / 3, c = rem - j * 3;
+                m[(c * Bp + b) * S + j] = v[k].x;        // Mr_c
+                m[((3 + c) * Bp + b) * S + j] = v[k].y;  // Mi_c
+            }
+        }
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mtiles = Lp / 16, ntiles = Bp / 8;
+    if (TC) {
+        // unit = (output matrix, m-tile); a warp accumulates all n-tiles of both positions
+        const int units = 6 * mtiles;
+        const int gr = lane >> 2, gc = lane & 3;
+        for (int unit = warp; unit < units; unit += kGemmThreads / 32) {
+            const int o = unit / mtiles, mt = unit - o * mtiles;
+            float acc[2][8][4];  // [position][n-tile <= 8][fragment]
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                for (int n = 0; n < 8; ++n)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) acc[q][n][f] = 0.f;
+            for (int t = 0; t < 3; ++t) {
+                const Term tm = c_terms[o][t];
+                const bool mirror = tm.comp == 3 || tm.comp == 5;
+                const float *A = Kd + (size_t)tm.comp * Lp * S + (mt * 16) * S;
+                for (int k0 = 0; k0 < Lp; k0 += 8) {
+                    const float a0 = A[gr * S + k0 + gc], a1 = A[(gr + 8) * S + k0 + gc];
+                    const float a2 = A[gr * S + k0 + gc + 4], a3 = A[(gr + 8) * S + k0 + gc + 4];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (q >= npos) break;
+                        const float sg = tm.sign * (mirror ? s_pos[q] : 1.f);
+                        uint32_t ah[4], al[4];
+                        const float av[4] = {sg * a0, sg * a1, sg * a2, sg * a3};
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            ah[f] = to_tf32(av[f]);
+                            al[f] = to_tf32(av[f] - __uint_as_float(ah[f]));
+                        }
+                        const float *Bm = Ms + ((size_t)q * 6 + tm.state) * Bp * S;
+#pragma unroll
+                        for (int n = 0; n < 8; ++n) {
+                            if (n >= ntiles) break;
+                            const float b0 = Bm[(n * 8 + gr) * S + k0 + gc];
+                            const float b1 = Bm[(n * 8 + gr) * S + k0 + gc + 4];
+                            uint32_t bh[2] = {to_tf32(b0), to_tf32(b1)};
+                            uint32_t bl[2] = {to_tf32(b0 - __uint_as_float(bh[0])),
+                                              to_tf32(b1 - __uint_as_float(bh[1]))};
+                            mma_tf32(acc[q][n], al, bh);
+                            mma_tf32(acc[q][n], ah, bl);
+                            mma_tf32(acc[q][n], ah, bh);
+                        }
+                    }
+                }
+            }
+            // results to the output area (spec2 is written after the final barrier)
+            float *Out = smem_f + 6 * Lp * S + 2 * 6 * Bp * S;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q >= npos) break;
+#pragma unroll
+                for (int n = 0; n < 8; ++n) {
+                    if (n >= ntiles) break;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        const int i = mt * 16 + gr + (f >= 2 ? 8 : 0);
+                        const int b = n * 8 + 2 * gc + (f & 1);
+                        Out[(((size_t)q * 6 + o) * Lp + i) * Bp + b] = acc[q][n][f];
+                    }
+                }
+            }
+        }
+    } else {
+        // CUDA cores: thread block of 4 rows x 4 states of one output matrix and position
+        const int rb = Lp / 4, cb = Bp / 4;
+        const int units = npos * 6 * rb * cb;
+        float *Out = smem_f + 6 * Lp * S + 2 * 6 * Bp * S;
+        for (int unit = threadIdx.x; unit < units; unit += kGemmThreads) {
+            int r = unit;
+            const int cbi = r % cb;
+            r /= cb;
+            const int rbi = r % rb;
+            r /= rb;
+            const int o = r % 6, q = r / 6;
+            float acc[4][4] = {};
+            for (int t = 0; t < 3; ++t) {
+                const Term tm = c_terms[o][t];
+                const bool mirror = tm.comp == 3 || tm.comp == 5;
+                const float sg = tm.sign * (mirror ? s_pos[q] : 1.f);
+                const float *A = Kd + (size_t)tm.comp * Lp * S + (rbi * 4) * S;
+                const float *Bm = Ms + ((size_t)q * 6 + tm.state) * Bp * S + (cbi * 4) * S;
+                for (int j = 0; j < Lp; ++j) {
+                    float av[4], bv[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        av[x] = sg * A[x * S + j];
+                        bv[x] = Bm[x * S + j];
+                    }
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y)
+                    Out[(((size_t)q * 6 + o) * Lp + rbi * 4 + x) * Bp + cbi * 4 + y] = acc[x][y];
+        }
+    }
+    __syncthreads();
+    // results: Out[pos][o][i][b] -> spec2 at the entry's positions, (re, im) pairs
+    const float *Out = smem_f + 6 * Lp * S + 2 * 6 * Bp * S;
+    for (int e = threadIdx.x; e < npos * planes; e += kGemmThreads) {
+        const int pos = e / planes, g = e - pos * planes;
+        const int b = g / (3 * L), rem = g - b * 3 * L, i = rem / 3, c = rem - i * 3;
+        const float re = Out[(((size_t)pos * 6 + 2 * c) * Lp + i) * Bp + b];
+        const float im = Out[(((size_t)pos * 6 + 2 * c + 1) * Lp + i) * Bp + b];
+        sk[(size_t)(pos ? p2 : p1) * planes + g] = make_float2(re, im);
+    }
+}
+
+}  // namespace demag
+
+namespace demag {
+
+cudaError_t launch_contract_gemm(const ApplyArgs &a, bool tensor_cores, cudaStream_t st) {
+    const int Py = 1 << a.log2Py, Qy = Py / 2 + 1, Kx = (1 << a.log2Px) / 2 + 1;
+    const size_t smem = gemm_smem_bytes(a.L, a.B);
+    cudaError_t e;
+    dim3 grid(Kx, Qy);
+    if (tensor_cores) {
+        if ((e = cudaFuncSetAttribute(k_contract_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_contract_gemm<true><<<grid, kGemmThreads, smem, st>>>((float2 *)a.spec2, (const float *)a.tensor,
+                                                               (const float *)a.ratio, a.L, a.B, a.log2Py,
+                                                               a.npairs);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_contract_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_contract_gemm<false><<<grid, kGemmThreads, smem, st>>>((float2 *)a.spec2, (const float *)a.tensor,
+                                                                (const float *)a.ratio, a.L, a.B, a.log2Py,
+                                                                a.npairs);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace demag

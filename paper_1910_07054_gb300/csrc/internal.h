@@ -57,11 +57,12 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
                                cudaStream_t st);
 
 // Extract the stored quadrant of pairs [p0, p0+np) from transformed planes into
-// the plan tensor [Kx][npairs][6][QyS] (float or double), scaled by 1/(Px Py),
-// y-frequencies in the stored order of layout.cuh.
+// the plan tensor, scaled by 1/(Px Py), y-frequencies in the stored order of
+// layout.cuh: [Kx][npairs][6][QyS] (umajor = 0) or [Kx][Qy][npairs][6]
+// (umajor = 1, float only).
 cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs,
                                   int log2Px, int log2Py, int QyS, void *tensor, bool fp64,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int umajor = 0);
 
 // ---- apply ---------------------------------------------------------------
 struct ApplyArgs {
@@ -77,10 +78,17 @@ struct ApplyArgs {
     void *spec2 = nullptr;  // split path: [Kx][Py][B][L][3] complex workspace
     int split = 0;        // 1: column transforms and contraction in separate kernels
     int full_pairs = 0;   // 1: tensor holds all L*L pairs (no reciprocity)
+    int contract_mode = 0;  // split path: 0 per-item kernel, 1 dense products on
+                            // FP32 cores, 2 dense products on tensor cores (3xTF32)
     const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
     double Ms;
 };
+
+// Dense-product contraction (contract_gemm.cu), float tensors in the u-major layout.
+size_t gemm_smem_bytes(int L, int B);
+bool gemm_supported(int L, int B);
+cudaError_t launch_contract_gemm(const ApplyArgs &a, bool tensor_cores, cudaStream_t st);
 
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);
@@ -107,6 +115,8 @@ struct demag_plan {
     void *d_spec = nullptr;       // [max_batch][L][3][Kx][ny] complex
     void *d_spec2 = nullptr;      // split path workspace
     int split = 0;                // 1: split path
+    int contract_mode = 0;        // split path contraction (see ApplyArgs)
+    int umajor = 0;               // tensor layout [Kx][Qy][npairs][6] (split-TF32 plans)
     void *d_tscale = nullptr;     // [2L]: t_l, then 1 / t_l (plan real type)
     void *d_dtensor = nullptr;    // d N / d t_dlayer, all L*L pairs, [Kx][L*L][6][QyS]
     int dlayer = -1;              // layer of d_dtensor (-1: none)

@@ -56,4 +56,8 @@ __host__ __device__ inline int tensor_row(int log2Py, bool fp64) {
     return (Qy + q - 1) / q * q;
 }
 
+// Floats per (kx, u) block of the u-major tensor layout: npairs * 6 padded to
+// 16 bytes so that every block starts on a 16-byte boundary.
+__host__ __device__ inline int umajor_block(int npairs) { return (npairs * 6 + 3) / 4 * 4; }
+
 }  // namespace demag

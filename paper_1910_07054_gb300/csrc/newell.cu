@@ -673,7 +673,7 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
 // FFT(N_yz) = i b.
 template <typename T>
 __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, int npairs,
-                          int log2Px, int log2Py, int QyS, T *__restrict__ tensor) {
+                          int log2Px, int log2Py, int QyS, T *__restrict__ tensor, int umajor) {
     const int Px = 1 << log2Px, Py = 1 << log2Py;
     const int Kx = Px / 2 + 1, Qy = Py / 2 + 1;
     const long long total = (long long)np * Kx * Qy;
@@ -686,25 +686,28 @@ __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, in
     const double2 *base = planes + (size_t)P * 3 * Px * Py + (size_t)kq * Px + kx;
     const double2 A = base[0], Bp = base[(size_t)Px * Py], C = base[(size_t)2 * Px * Py];
     const double sc = 1.0 / ((double)Px * (double)Py);
-    T *o = tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * QyS + u;
-    o[0 * QyS] = (T)(A.x * sc);
-    o[1 * QyS] = (T)(A.y * sc);
-    o[2 * QyS] = (T)(Bp.x * sc);
-    o[3 * QyS] = (T)(Bp.y * sc);
-    o[4 * QyS] = (T)(C.y * sc);
-    o[5 * QyS] = (T)(-C.x * sc);
+    const size_t cs = umajor ? 1 : QyS;  // component stride
+    T *o = umajor ? tensor + ((size_t)kx * Qy + u) * umajor_block(npairs) + (size_t)(p0 + P) * 6
+                  : tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * QyS + u;
+    o[0 * cs] = (T)(A.x * sc);
+    o[1 * cs] = (T)(A.y * sc);
+    o[2 * cs] = (T)(Bp.x * sc);
+    o[3 * cs] = (T)(Bp.y * sc);
+    o[4 * cs] = (T)(C.y * sc);
+    o[5 * cs] = (T)(-C.x * sc);
 }
 
 cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs, int log2Px,
-                                  int log2Py, int QyS, void *tensor, bool fp64, cudaStream_t st) {
+                                  int log2Py, int QyS, void *tensor, bool fp64, cudaStream_t st,
+                                  int umajor) {
     const long long total = (long long)np * ((1 << log2Px) / 2 + 1) * ((1 << log2Py) / 2 + 1);
     const unsigned grid = (unsigned)((total + 255) / 256);
     if (fp64)
         k_extract<double><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
-                                                (double *)tensor);
+                                                (double *)tensor, umajor);
     else
         k_extract<float><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
-                                               (float *)tensor);
+                                               (float *)tensor, umajor);
     return cudaGetLastError();
 }
 

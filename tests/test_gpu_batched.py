@@ -1,0 +1,76 @@
+"""GPU parity of the batched, many-layer contraction (DEMAG_PREC_SPLIT_TF32):
+the dense-product contraction on the tensor cores (three TF32 passes, path 4)
+and the same products on the FP32 cores (path 3), against the oracle.
+
+Tolerance: 1e-5 relative L2 against the float64 oracle for both (the
+library's float32 target); the two variants within 3e-6 of each other.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1910_07054_gb300 as dm
+from oracle import demag as odm
+from oracle import newell as onw
+from paper_1910_07054_gb300 import inputs
+from _cases import reading_kernels, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def _fields(plan, m, Ms, paths):
+    out = {}
+    mt = torch.tensor(m, dtype=torch.float32, device="cuda")
+    for path in paths:
+        dm.demag_plan_set_path(plan.handle, path)
+        plan.info = dm.demag_plan_info(plan.handle)
+        H = plan.apply(mt, Ms)
+        torch.cuda.synchronize()
+        out[path] = H.double().cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,th,B", [
+    (48, 40, tuple(np.round(np.linspace(0.5, 3.0, 16), 3)), 8),   # tiles without padding
+    (21, 13, (1.0, 0.5, 2.0, 0.8, 1.7), 3),                        # L and B padded
+    (32, 32, tuple(np.round(np.linspace(2.5, 0.6, 32), 3)), 16),
+])
+def test_split_tf32_matches_oracle(nx, ny, th, B):
+    m = inputs.random_unit_vectors((B, len(th), ny, nx), seed=len(th) + B)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    assert plan.info["path"] == 4
+    H = _fields(plan, m, 8e5, (4, 3))
+    plan.close()
+    K = reading_kernels(nx, ny, 2.0, 2.0, th)
+    ref = odm.hybrid(K, m, 8e5)
+    assert rel_l2(H[4], ref) < 1e-5
+    assert rel_l2(H[3], ref) < 1e-5
+    assert rel_l2(H[4], H[3]) < 3e-6
+
+
+def test_scale512_batch_sampled_against_oracle():
+    """512 x 512 cells, 64 layers, 16 states: both contraction variants agree at
+    full size, and one target layer of one state is checked against the oracle
+    (computed pair by pair)."""
+    c = inputs.CONFIGS["scale512"]
+    nx, ny, B = c["nx"], c["ny"], c["batch"]
+    th = inputs.thicknesses("scale512")
+    L = len(th)
+    m = inputs.random_unit_vectors((B, L, ny, nx), seed=0)
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], tuple(th), precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    H = _fields(plan, m, inputs.MS_DEFAULT, (4, 3))
+    plan.close()
+    assert rel_l2(H[4], H[3]) < 3e-6
+    target, state = 37, 5
+    ref = odm.hybrid_targets(lambda i, j: onw.pair_kernel(nx, ny, c["dx"], c["dy"], th, i, j),
+                             m[state], inputs.MS_DEFAULT, [target])[target]
+    assert rel_l2(H[4][state, target], ref) < 1e-5
+    assert rel_l2(H[3][state, target], ref) < 1e-5

@@ -132,3 +132,14 @@ def test_safm_worked_example_optimum():
     tol = 0.5 * 10.0 ** (-gold["printed_digits"])
     assert abs(t - gold["optimum_middle_nm"]) <= tol
     assert abs(_safm_mean_hz(t)) < 1e-8
+
+
+def test_target_layer_hybrid_equals_full_hybrid():
+    """The pair-by-pair restriction to selected target layers (used at sizes
+    where all L x L kernels do not fit memory) is the same Eq. FFT_v2."""
+    nx, ny, th = 6, 5, [1.0, 0.5, 2.0, 0.7]
+    K = nw.layer_kernels(nx, ny, 2.0, 2.0, th, mode=nw.READING_D, full=True)
+    m = inputs.random_unit_vectors((len(th), ny, nx), seed=14)
+    H = dm.hybrid(K, m, 3.0)
+    Ht = dm.hybrid_targets(lambda i, j: nw.pair_kernel(nx, ny, 2.0, 2.0, th, i, j), m, 3.0, [0, 3])
+    assert np.abs(Ht[0] - H[0]).max() == 0.0 and np.abs(Ht[3] - H[3]).max() == 0.0
