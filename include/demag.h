@@ -312,6 +312,52 @@ demag_status demag_apply_static(const void *tensor, const double *thickness, int
 demag_status demag_tensor_points_dt(int n, const double *geom, double *out, double *dout,
                                     void *stream);
 
+/*
+ * Surrogate network for the thickness optimisation of Sec. 4 (the paper runs
+ * Newton on one layer thickness to zero the mean z-field of the free layer;
+ * the surrogate proposes those steps and the solver accepts or rejects them).
+ *
+ * A multilayer perceptron with I inputs, three tanh hidden layers of H units
+ * and O linear outputs (I <= 32, H <= 64, O <= 8):
+ *   h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3),
+ *   y = W4 h3 + b4.
+ * Parameters form one vector of demag_mlp_param_count(I, H, O) values:
+ *   W1 [H][I], b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], W4 [O][H], b4 [O]
+ * (row-major W[out][in]).  Compute reads them as bfloat16 (w_bf16, DEVICE,
+ * 16-bit values) and accumulates in float; the optimiser keeps a float master
+ * copy.  x: DEVICE float [N][I]; y, gy: DEVICE float [N][O].
+ */
+int demag_mlp_param_count(int I, int H, int O);
+
+/* y = network(x) for N samples. */
+demag_status demag_mlp_forward(const void *w_bf16, const float *x, float *y, int N, int I, int H,
+                               int O, void *stream);
+
+/*
+ * Back-propagation of gy = dLoss/dy through the network at x:
+ *   gw (DEVICE float [P], may be NULL): dLoss/dparameters ADDED to gw;
+ *   gx (DEVICE float [N][I], may be NULL): dLoss/dx written.
+ */
+demag_status demag_mlp_backward(const void *w_bf16, const float *x, const float *gy, float *gw,
+                                float *gx, int N, int I, int H, int O, void *stream);
+
+/* Mean squared error: *loss (DEVICE double) += sum (y - target)^2 / N;
+ * gy = 2 (y - target) / N. */
+demag_status demag_mlp_mse(const float *y, const float *target, float *gy, double *loss, int N, int O,
+                           void *stream);
+
+/* One Adam step on the float master weights w (DEVICE float [P]) with moments
+ * m1, m2 and gradient g; refreshes w_bf16 (round to nearest even) and sets g
+ * to zero.  step >= 1 is the bias-correction count. */
+demag_status demag_mlp_adam(float *w, void *w_bf16, float *g, float *m1, float *m2, int P, float lr,
+                            float beta1, float beta2, float eps, int step, void *stream);
+
+/* out (DEVICE double [B][3]) = mean over the ny x nx cells of layer `layer` of
+ * the field H ([B][L][3][ny][nx], float or double by precision): the mean
+ * free-layer field the surrogate learns (Sec. 4's objective). */
+demag_status demag_layer_mean(const void *H, int precision, int B, int L, int ny, int nx, int layer,
+                              double *out, void *stream);
+
 /* demag_destroy - free a plan (NULL is accepted).  Synchronises the device. */
 demag_status demag_destroy(demag_plan_t plan);
 

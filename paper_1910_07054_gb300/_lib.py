@@ -72,6 +72,19 @@ def lib():
     L.demag_tensor_points_dt.restype = i
     L.demag_apply_static.argtypes = [vp, dp, i, i, i, i, vp, d, vp, i, vp]
     L.demag_apply_static.restype = i
+    f = ctypes.c_float
+    L.demag_mlp_param_count.argtypes = [i, i, i]
+    L.demag_mlp_param_count.restype = i
+    L.demag_mlp_forward.argtypes = [vp, vp, vp, i, i, i, i, vp]
+    L.demag_mlp_forward.restype = i
+    L.demag_mlp_backward.argtypes = [vp, vp, vp, vp, vp, i, i, i, i, vp]
+    L.demag_mlp_backward.restype = i
+    L.demag_mlp_mse.argtypes = [vp, vp, vp, vp, i, i, vp]
+    L.demag_mlp_mse.restype = i
+    L.demag_mlp_adam.argtypes = [vp, vp, vp, vp, vp, i, f, f, f, f, i, vp]
+    L.demag_mlp_adam.restype = i
+    L.demag_layer_mean.argtypes = [vp, i, i, i, i, i, i, vp, vp]
+    L.demag_layer_mean.restype = i
     L.demag_destroy.argtypes = [vp]
     L.demag_destroy.restype = i
     _lib = L
@@ -261,6 +274,47 @@ def demag_apply_static(tensor, thickness, nx, ny, precision, m, Ms, H, stream=No
                                     float(Ms), ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)),
            "demag_apply_static")
     return H
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def demag_mlp_param_count(I, H, O):
+    return int(lib().demag_mlp_param_count(int(I), int(H), int(O)))
+
+
+def demag_mlp_forward(w_bf16, x, y, I, H, O, stream=None):
+    """y[N, O] = network(x[N, I]); w_bf16: CUDA bfloat16 [P]."""
+    _check(lib().demag_mlp_forward(_ptr(w_bf16), _ptr(x), _ptr(y), int(x.shape[0]), int(I), int(H), int(O),
+                                   _stream(stream)), "demag_mlp_forward")
+    return y
+
+
+def demag_mlp_backward(w_bf16, x, gy, gw, gx, I, H, O, stream=None):
+    """gw += dLoss/dparameters (if not None); gx = dLoss/dx (if not None)."""
+    _check(lib().demag_mlp_backward(_ptr(w_bf16), _ptr(x), _ptr(gy), _ptr(gw), _ptr(gx), int(x.shape[0]),
+                                    int(I), int(H), int(O), _stream(stream)), "demag_mlp_backward")
+
+
+def demag_mlp_mse(y, target, gy, loss, stream=None):
+    """loss (CUDA float64 [1]) += mean squared error; gy = its gradient in y."""
+    _check(lib().demag_mlp_mse(_ptr(y), _ptr(target), _ptr(gy), _ptr(loss), int(y.shape[0]), int(y.shape[1]),
+                               _stream(stream)), "demag_mlp_mse")
+
+
+def demag_mlp_adam(w, w_bf16, g, m1, m2, lr, beta1, beta2, eps, step, stream=None):
+    _check(lib().demag_mlp_adam(_ptr(w), _ptr(w_bf16), _ptr(g), _ptr(m1), _ptr(m2), int(w.numel()), float(lr),
+                                float(beta1), float(beta2), float(eps), int(step), _stream(stream)),
+           "demag_mlp_adam")
+
+
+def demag_layer_mean(H, precision, layer, out, stream=None):
+    """out (CUDA float64 [B, 3]) = mean over the cells of layer `layer` of H [B, L, 3, ny, nx]."""
+    B, L, _, ny, nx = H.shape
+    _check(lib().demag_layer_mean(_ptr(H), int(precision), int(B), int(L), int(ny), int(nx), int(layer),
+                                  _ptr(out), _stream(stream)), "demag_layer_mean")
+    return out
 
 
 def demag_destroy(plan):

@@ -146,7 +146,8 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
                 break;
             }
             e = layer < 0 ? launch_kernel_planes(planes, p0, np, d_pi, d_pj, p->nx, p->ny, p->dx, p->dy,
-                                                 p->log2Px, p->log2Py, d_z, d_th, st)
+                                                 p->log2Px, p->log2Py, d_z, d_th, st,
+                                                 p->precision != DEMAG_PREC_FP64)
                           : launch_dkernel_planes(planes, p0, np, L, layer, p->nx, p->ny, p->dx, p->dy,
                                                   p->log2Px, p->log2Py, d_z, d_th, st);
             if (e != cudaSuccess) {

@@ -35,10 +35,11 @@ cudaError_t launch_tensor_points(int n, const double *geom, double *out, cudaStr
 // Fill the padded real-space kernels of pairs [p0, p0 + np) into three complex
 // double planes per pair ([np][3][Py][Px], x fastest), zeroed beforehand:
 // plane 0 = N_xx + i N_yy, plane 1 = N_zz + i N_xy, plane 2 = N_xz + i N_yz.
+// far32: far-field quadrature with float node sums (float plans).
 cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pair_i,
                                  const int *pair_j, int nx, int ny, double dx, double dy,
                                  int log2Px, int log2Py, const double *z, const double *th,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool far32 = false);
 
 // Tensor and its derivative along (dtz, dsz, dZ) at geom[n][12]
 // (X,Y,Z,tx,ty,tz,sx,sy,sz,dtz,dsz,dZ) -> out[n][6], dout[n][6].

@@ -301,11 +301,73 @@ __device__ __forceinline__ int far_nodes(double rho) {
     return rho >= 128.0 ? 3 : rho >= 32.0 ? 4 : rho >= 11.0 ? 5 : rho >= 5.5 ? 6 : rho >= 2.75 ? 7 : 8;
 }
 
+// Float plans: the far field carries no cancellation, so its quadrature runs
+// in float with nodes chosen for ~3e-8 of the largest component (below the
+// float rounding of the stored tensor).
+__device__ __forceinline__ int far_nodes_f32(double rho) {
+    return rho >= 64.0 ? 2 : rho >= 11.0 ? 3 : rho >= 4.0 ? 4 : rho >= 2.75 ? 5 : 6;
+}
+
+constexpr int kF32AxisMax = 64;
+
+// The quadrature of quadrature_tensor with the node sums in float.  Returns
+// false (nothing written) if an axis needs more than kF32AxisMax nodes.
+__device__ bool quadrature_tensor_f32(double X, double Y, double Z, const double t[3],
+                                      const double s[3], int n, double wcap, double out[6]) {
+    AxisRule rx, ry, rz;
+    axis_rule(rx, t[0], s[0], wcap, n);
+    axis_rule(ry, t[1], s[1], wcap, n);
+    axis_rule(rz, t[2], s[2], wcap, n);
+    if (rx.count > kF32AxisMax || ry.count > kF32AxisMax || rz.count > kF32AxisMax) return false;
+    float zd[kF32AxisMax], zw[kF32AxisMax];
+    for (int k = 0; k < rz.count; ++k) {
+        double u, w;
+        axis_node(rz, n, k, u, w);
+        zd[k] = (float)(Z + u);
+        zw[k] = (float)w;
+    }
+    float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+    for (int kx = 0; kx < rx.count; ++kx) {
+        double ux, wx;
+        axis_node(rx, n, kx, ux, wx);
+        const float dxv = (float)(X + ux);
+        for (int ky = 0; ky < ry.count; ++ky) {
+            double uy, wy;
+            axis_node(ry, n, ky, uy, wy);
+            const float dyv = (float)(Y + uy);
+            const float wxy = (float)(wx * wy);
+            const float rxy = dxv * dxv + dyv * dyv;
+            for (int kz = 0; kz < rz.count; ++kz) {
+                const float dzv = zd[kz];
+                const float r2 = rxy + dzv * dzv;
+                const float ir = rsqrtf(r2);
+                const float ir2 = ir * ir;
+                const float q = wxy * zw[kz] * ir * ir2 * ir2;
+                const float q3 = 3.f * q;
+                hxx += q3 * dxv * dxv - q * r2;
+                hyy += q3 * dyv * dyv - q * r2;
+                hzz += q3 * dzv * dzv - q * r2;
+                hxy += q3 * dxv * dyv;
+                hxz += q3 * dxv * dzv;
+                hyz += q3 * dyv * dzv;
+            }
+        }
+    }
+    const double sc = -1.0 / (4.0 * kPi * t[0] * t[1] * t[2]);
+    out[0] = hxx * sc;
+    out[1] = hyy * sc;
+    out[2] = hzz * sc;
+    out[3] = hxy * sc;
+    out[4] = hxz * sc;
+    out[5] = hyz * sc;
+    return true;
+}
+
 // The evaluation used everywhere: closed form while the gap between the two
 // cuboids is below the larger in-plane edge, quadrature (sub-pieces no wider
 // than half the gap) beyond.
 __device__ void tensor_eval(double X, double Y, double Z, const double t[3], const double s[3],
-                            double out[6]) {
+                            double out[6], bool far32 = false) {
     const double o[3] = {X, Y, Z};
     double gap2 = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -328,6 +390,7 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
         for (int p = 0; p < 3; ++p)
             if (ws[p] > 0.0) widest = fmax(widest, ws[p] / ceil(ws[p] / wcap));
     }
+    if (far32 && quadrature_tensor_f32(X, Y, Z, t, s, far_nodes_f32(gap / widest), wcap, out)) return;
     quadrature_tensor(X, Y, Z, t, s, far_nodes(gap / widest), wcap, out);
 }
 
@@ -490,7 +553,8 @@ cudaError_t launch_tensor_points(int n, const double *geom, double *out, cudaStr
 __global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
                                 const int *__restrict__ pair_i, const int *__restrict__ pair_j,
                                 int nx, int ny, double dx, double dy, int log2Px, int log2Py,
-                                const double *__restrict__ z, const double *__restrict__ th) {
+                                const double *__restrict__ z, const double *__restrict__ th,
+                                int far32) {
     const long long total = (long long)np * nx * ny;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -500,7 +564,7 @@ __global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
     const int i = pair_i[p0 + P], j = pair_j[p0 + P];
     const double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
     double N[6];
-    tensor_eval(p * dx, q * dy, z[i] - z[j], t, s, N);
+    tensor_eval(p * dx, q * dy, z[i] - z[j], t, s, N, far32 != 0);
     const int Px = 1 << log2Px, Py = 1 << log2Py;
     double2 *base = planes + (size_t)P * 3 * Px * Py;
     for (int my = 0; my < 2; ++my) {
@@ -591,11 +655,11 @@ cudaError_t launch_dkernel_planes(double2 *planes, int p0, int np, int L, int la
 cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pair_i,
                                  const int *pair_j, int nx, int ny, double dx, double dy,
                                  int log2Px, int log2Py, const double *z, const double *th,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool far32) {
     const long long total = (long long)np * nx * ny;
     const int bs = 128;
     k_kernel_planes<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(
-        planes, p0, np, pair_i, pair_j, nx, ny, dx, dy, log2Px, log2Py, z, th);
+        planes, p0, np, pair_i, pair_j, nx, ny, dx, dy, log2Px, log2Py, z, th, far32 ? 1 : 0);
     return cudaGetLastError();
 }
 

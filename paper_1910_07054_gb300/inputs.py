@@ -85,3 +85,52 @@ def safm_stack(t_middle, n=64, diameter=60.0):
     m[0, 2][mask] = 1.0
     m[2, 2][mask] = -1.0
     return dx, th, m
+
+
+def bf16_round(x):
+    """Round float32 values to bfloat16 (nearest, ties to even).  Returns the
+    rounded values as float32 and their 16-bit patterns (uint16)."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    bits = a.view(np.uint32).astype(np.uint64)
+    lsb = (bits >> 16) & 1
+    rounded = ((bits + 0x7FFF + lsb) >> 16).astype(np.uint16)
+    back = (rounded.astype(np.uint32) << 16).view(np.float32)
+    return back, rounded
+
+
+def mlp_init(I, H, O, seed):
+    """Seeded initial parameters (uniform, fan-in scaled), flat float32 vector."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((H, I), (H, H), (H, H), (O, H)):
+        lim = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(rng.uniform(-lim, lim, size=fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+# Sec. 4-like optimisation stack on the MRAM-like thicknesses (1-based layers):
+# layers 1, 3 pinned +z and layer 5 pinned -z inside the disk inscribed in
+# the grid; layers 2, 4, 6, 7 spacers; layer 8 the free layer (m = 0), whose
+# mean z-field is the objective; layer 5's thickness is the design variable.
+OPT_BASE = np.array([1.0, 0.8, 1.2, 0.9, 5.0, 1.5, 0.7, 2.0])
+OPT_LAYER = 4   # 0-based index of layer 5
+FREE_LAYER = 7  # 0-based index of layer 8
+
+
+def opt_stack_magnetization(n):
+    mask = disk_mask(n, n)
+    m = np.zeros((len(OPT_BASE), 3, n, n))
+    m[0, 2][mask] = 1.0
+    m[2, 2][mask] = 1.0
+    m[4, 2][mask] = -1.0
+    return m
+
+
+def opt_samples(count, seed, t5_range=(0.5, 5.0), jitter=0.10):
+    """Thickness sets: layer 5 uniform in t5_range, the others the base values
+    jittered uniformly by +-jitter (relative)."""
+    rng = np.random.default_rng(seed)
+    t = OPT_BASE[None, :] * (1.0 + rng.uniform(-jitter, jitter, size=(count, len(OPT_BASE))))
+    t[:, OPT_LAYER] = rng.uniform(t5_range[0], t5_range[1], size=count)
+    return t
