@@ -41,6 +41,8 @@ def parse_args():
                    help="seconds of oracle evaluation for the CPU baseline sample")
     p.add_argument("--no-parity", action="store_true", help="skip the oracle field comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched (512x512x64, 16 states) and surrogate measurements")
     return p.parse_args()
 
 
@@ -208,6 +210,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_measurement(steps, peaks):
+    """512 x 512 cells, 64 layers, 16 states per apply: the split-precision
+    tensor-core contraction (path 4) against the same products on the FP32
+    cores (path 3), same plan, same data movement."""
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import inputs
+    c = inputs.CONFIGS["scale512"]
+    th = [float(t) for t in inputs.thicknesses("scale512")]
+    nx, ny, B, L = c["nx"], c["ny"], c["batch"], len(th)
+    t0 = time.perf_counter()
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    m = torch.tensor(inputs.random_unit_vectors((B, L, ny, nx), seed=0), dtype=torch.float32, device="cuda")
+    H = torch.empty_like(m)
+    out = {"workload": "512x512 cells of 2x2 nm, 64 layers (t ~ U[0.5, 3] nm, seed 0), 16 random "
+                       "states per apply; inputs (3.2 GB) exceed L2", "plan_create_s": build_s}
+    fields = {}
+    for path, name in ((4, "tensor_cores_3xtf32"), (3, "fp32_cores")):
+        dm.demag_plan_set_path(plan.handle, path)
+        info = dm.demag_plan_info(plan.handle)
+        dm.demag_apply(plan.handle, m, inputs.MS_DEFAULT, H, info=info)
+        st = np.mean([dm.demag_apply_timed(plan.handle, m, inputs.MS_DEFAULT, H, info=info)
+                      for _ in range(steps)], axis=0)
+        total = float(st[0] + st[1] + st[2])
+        fields[path] = H.clone()
+        flops = 36.0 * L * L * B * (nx + 1) * (2 * ny)  # useful contraction flops per apply
+        out[name] = {"states_per_s": B / (total * 1e-3), "ms_per_apply": total,
+                     "kernels_ms": {"rows_forward": float(st[0]), "columns_forward": float(st[3]),
+                                    "contraction": float(st[4]), "columns_inverse": float(st[5]),
+                                    "rows_inverse": float(st[2])},
+                     "contraction_tflops_useful": flops / (st[4] * 1e-3) / 1e12}
+    tf32_peak = peaks.get("bf16_tflops", 1894.6) * (1.1 / 2.25)
+    tc = out["tensor_cores_3xtf32"]
+    tc["roofline"] = {"bound": "tensor", "achieved": 3 * tc["contraction_tflops_useful"],
+                      "peak": tf32_peak, "unit": "TFLOP/s",
+                      "frac": 3 * tc["contraction_tflops_useful"] / tf32_peak,
+                      "note": "TF32 issue rate (3 passes per useful flop) against the measured bf16 "
+                              "burst peak x nominal tf32/bf16 ratio (1.1/2.25)"}
+    d = fields[4] - fields[3]
+    out["rel_l2_between_variants"] = float(torch.linalg.vector_norm(d.double()) /
+                                           torch.linalg.vector_norm(fields[3].double()))
+    out["speedup_tensor_vs_fp32_cores"] = out["fp32_cores"]["ms_per_apply"] / tc["ms_per_apply"]
+    plan.close()
+    return out
+
+
+def surrogate_measurement():
+    """Sec. 4-like optimisation on the 256 x 256 x 8 stack: 2000 solver samples
+    (layer 5 in [0.5, 5] nm, the others +-10%), network training, and Newton on
+    the layer-5 thickness from 5 nm, exact vs surrogate-proposed steps."""
+    import numpy as np
+
+    from paper_1910_07054_gb300 import inputs
+    from paper_1910_07054_gb300 import surrogate as sg
+    solver = sg.ExactSolver(256, 2.0)
+    t0 = time.perf_counter()
+    T, Y = sg.generate_samples(solver, inputs.opt_samples(2000, seed=0))
+    gen_s = time.perf_counter() - t0
+    net = sg.Surrogate(seed=0)
+    t0 = time.perf_counter()
+    hist = net.fit(T[:1800], Y[:1800], steps=4000, lr=3e-3)
+    fit_s = time.perf_counter() - t0
+    held = net.predict(T[1800:])[:, 2]
+    rmse = float(np.sqrt(np.mean((held - Y[1800:, 2]) ** 2)))
+    start = inputs.OPT_BASE.copy()
+    solver.solves = 0
+    ex = sg.newton_exact(solver, start, tol=1e-6)
+    solver.solves = 0
+    su = sg.newton_surrogate(solver, net, start, tol=1e-6)
+    t_star = ex[-1][0]
+    n_ex = next(h[2] for h in ex if abs(h[0] - t_star) < 1e-3)
+    n_su = next(h[2] for h in su if abs(h[0] - t_star) < 1e-3)
+    return {"samples": 2000, "sample_generation_s": gen_s, "train_s": fit_s, "final_loss": hist[-1][1],
+            "heldout_rmse_hz_over_ms": rmse, "t_opt_nm": t_star,
+            "exact_solves_to_1e-3nm": {"newton_exact_adjoint": n_ex, "surrogate_proposed": n_su},
+            "surrogate_final_t_nm": su[-1][0]}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -273,7 +357,7 @@ def run_ours(args):
     stage = np.zeros(3)
     for k in range(nk):
         flush.fill_(float(k))
-        stage += np.array(dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info))
+        stage += np.array(dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info)[:3])
     stage /= nk
 
     # end to end through the host entry point (pinned buffers, copies included)
@@ -298,6 +382,17 @@ def run_ours(args):
     peak, peak_kind = measured_hbm_peak()
     achieved = stage_bytes[dom] / (stage[dom] * 1e-3) / 1e9
     traffic = recorded_traffic(names[dom])
+
+    extras = {}
+    if world == 1 and not args.no_extras:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
+                os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as fh:
+            try:
+                peaks = json.load(fh)
+            except ValueError:
+                peaks = {}
+        extras["batched"] = batched_measurement(3, peaks)
+        extras["surrogate"] = surrogate_measurement()
 
     line = None
     if rank == 0:
@@ -339,6 +434,8 @@ def run_ours(args):
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "plan_create_s": plan_s,
+            "batched": extras.get("batched"),
+            "surrogate": extras.get("surrogate"),
             "wall_s_timed_loop": wall,
         }
     plan.close()

@@ -210,7 +210,10 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
  * kernel, then synchronises the stream and writes the elapsed times:
  *   stage_ms (HOST, nstage values, nstage >= 3):
  *     [0] forward row transforms, [1] column transforms + layer contraction,
- *     [2] inverse row transforms (milliseconds, CUDA event resolution).
+ *     [2] inverse row transforms (milliseconds, CUDA event resolution);
+ *     with nstage >= 6 on a plan running the split path (2, 3, 4) also
+ *     [3] forward column transforms, [4] layer contraction, [5] inverse
+ *     column transforms (the parts of [1]); zero otherwise.
  * Other arguments as in demag_apply.
  */
 demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void *H, int B,

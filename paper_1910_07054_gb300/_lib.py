@@ -217,14 +217,15 @@ def demag_tensor_points_dt(geom, out, dout, stream=None):
 
 
 def demag_apply_timed(plan, m, Ms, H, stream=None, info=None):
-    """demag_apply with per-kernel event times; returns [rows fwd, columns, rows inv] in ms."""
+    """demag_apply with per-kernel event times (ms): [rows fwd, columns, rows inv,
+    and for split plans: column fwd, contraction, column inv (else 0)]."""
     info = info or demag_plan_info(plan)
     B = _field_check(m, info, "m")
     if _field_check(H, info, "H") != B or H.shape != m.shape:
         raise ValueError("H must have the shape of m")
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * 6)()
     _check(lib().demag_apply_timed(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
-                                   ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream), ms, 3),
+                                   ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream), ms, 6),
            "demag_apply_timed")
     return [float(v) for v in ms]
 

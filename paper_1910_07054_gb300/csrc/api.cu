@@ -391,17 +391,24 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
     demag_status rc = check_apply(plan, m, Ms, H, B);
     if (rc != DEMAG_OK) return rc;
     if (!stage_ms || nstage < kApplyStages) return fail(DEMAG_EINVAL, "stage_ms must hold 3 values");
-    cudaEvent_t ev[kApplyStages + 1] = {};
+    const bool inner = nstage >= kApplyStages + 3 && plan->split;
+    const int nev = kApplyStages + 1 + (inner ? 4 : 0);
+    cudaEvent_t ev[kApplyStages + 5] = {};
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     int made = 0;
-    for (; made <= kApplyStages; ++made)
+    for (; made < nev; ++made)
         if ((e = cudaEventCreate(&ev[made])) != cudaSuccess) break;
-    if (e == cudaSuccess)
-        e = launch_apply(apply_args(plan, Ms, B), m, H, plan->precision == DEMAG_PREC_FP64, st, ev);
+    ApplyArgs a = apply_args(plan, Ms, B);
+    if (inner) a.inner_ev = ev + kApplyStages + 1;
+    if (e == cudaSuccess) e = launch_apply(a, m, H, plan->precision == DEMAG_PREC_FP64, st, ev);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (int k = 0; e == cudaSuccess && k < kApplyStages; ++k)
         e = cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]);
+    for (int k = 0; e == cudaSuccess && inner && k < 3; ++k)
+        e = cudaEventElapsedTime(&stage_ms[kApplyStages + k], ev[kApplyStages + 1 + k],
+                                 ev[kApplyStages + 2 + k]);
+    for (int k = kApplyStages; k < nstage && !inner; ++k) stage_ms[k] = 0.0f;
     for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(e, "demag_apply_timed");
     return DEMAG_OK;

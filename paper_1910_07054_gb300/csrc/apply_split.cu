@@ -268,16 +268,22 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
                                   (int)smem_col)) != cudaSuccess)
         return e;
     dim3 gcol(Kx, (planes + G - 1) / G);
+    cudaEvent_t *iev = a.inner_ev;
+    if (iev && (e = cudaEventRecord(iev[0], st)) != cudaSuccess) return e;
     k_columns_forward<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec, (C *)a.spec2, a.ny,
                                                                 Kx, planes, G, a.log2Py,
                                                                 (const C *)a.twy, a.log2twy);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (iev && (e = cudaEventRecord(iev[1], st)) != cudaSuccess) return e;
     if (a.contract_mode != 0) {
         if ((e = launch_contract_gemm(a, a.contract_mode == 2, st)) != cudaSuccess) return e;
+        if (iev && (e = cudaEventRecord(iev[2], st)) != cudaSuccess) return e;
         k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec,
                                                                     a.ny, Kx, planes, G, a.log2Py,
                                                                     (const C *)a.twy, a.log2twy);
-        return cudaGetLastError();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (iev && (e = cudaEventRecord(iev[3], st)) != cudaSuccess) return e;
+        return cudaSuccess;
     }
     const int TU = split_tile<T>(a.L, a.B, 200 * 1024);
     const size_t smem_ct = (size_t)TU * 2 * planes * sizeof(C);
@@ -290,10 +296,13 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
                                                        (const T *)a.ratio, a.L, a.B, a.log2Py,
                                                        a.npairs, a.QyS, TU, a.full_pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (iev && (e = cudaEventRecord(iev[2], st)) != cudaSuccess) return e;
     k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec, a.ny,
                                                                 Kx, planes, G, a.log2Py,
                                                                 (const C *)a.twy, a.log2twy);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (iev && (e = cudaEventRecord(iev[3], st)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 cudaError_t launch_split_columns(const ApplyArgs &a, bool fp64, cudaStream_t st) {

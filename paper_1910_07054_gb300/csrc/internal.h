@@ -81,6 +81,7 @@ struct ApplyArgs {
     int full_pairs = 0;   // 1: tensor holds all L*L pairs (no reciprocity)
     int contract_mode = 0;  // split path: 0 per-item kernel, 1 dense products on
                             // FP32 cores, 2 dense products on tensor cores (3xTF32)
+    cudaEvent_t *inner_ev = nullptr;  // split path, optional [4]: before and after its 3 kernels
     const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
     double Ms;
