@@ -135,7 +135,7 @@ def measured_hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("apply.cu", "fft.cuh"):
+    for name in ("apply.cu", "apply512.cu", "fft.cuh", "fft8.cuh"):
         with open(os.path.join(ROOT, "paper_1910_07054_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,7 +377,9 @@ def run_ours(args):
     spec = B * L * 3 * Kx * ny * 8
     tensor = Kx * npairs * 6 * Qy * 4
     stage_bytes = [field + spec, 2 * spec + tensor, spec + field]
-    names = ["k_rows_forward", "k_columns_fused", "k_rows_inverse"]
+    r8 = "8" if info["Px"] == 512 else ""
+    names = ["k_rows_forward" + r8, "k_columns_fused" + ("8" if info["path"] == 5 else ""),
+             "k_rows_inverse" + r8]
     dom = int(np.argmax(stage))
     peak, peak_kind = measured_hbm_peak()
     achieved = stage_bytes[dom] / (stage[dom] * 1e-3) / 1e9

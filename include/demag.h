@@ -132,8 +132,12 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
  *           contraction as dense L x L by L x B products on the FP32 cores.
  *   path 4: (DEMAG_PREC_SPLIT_TF32 plans, their default) the same products
  *           on the tensor cores in three TF32 passes.
- *   path 0: the default choice of demag_plan_create (1 when it fits, else 2;
- *           4 for DEMAG_PREC_SPLIT_TF32).
+ *   path 5: (reported, not selectable otherwise) the fused column kernel with
+ *           the radix-8 512-point transforms, chosen by demag_plan_create
+ *           when Py = 512 and the columns fit; its tensor is stored in
+ *           natural folded-ky order, so such a plan runs path 5 only.
+ *   path 0: the default choice of demag_plan_create (5 or 1 when it fits,
+ *           else 2; 4 for DEMAG_PREC_SPLIT_TF32).
  * Both paths compute the same field (Eq. FFT_v2); this entry point exists to
  * test and time them against each other.  Errors: DEMAG_EINVAL, DEMAG_ENOMEM,
  * DEMAG_EUNSUPPORTED (the path cannot hold this plan).
@@ -224,7 +228,8 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
  *
  * out (HOST, 10 values): {nx, ny, L, Px, Py, precision, max_batch,
  *                         number of stored layer pairs, stored row length QyS,
- *                         column path: 1 fused, 2 split}
+ *                         column path: 1 fused, 2 split, 3/4 split-TF32
+ *                         variants, 5 fused 512-point}
  * Px, Py are the padded FFT sizes; the stored tensor holds the layer pairs
  * i <= j (the rest follow from reciprocity, t_i N(i<-j)(d) = t_j N(j<-i)(-d)).
  */
@@ -244,7 +249,9 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
  * the y-frequency ky(u) = min(k, Py - k), k = bitrev(p1(u)) over log2(Py)
  * bits, where p1(0) = 0, p1(1) = 1 and, for u in [2^(m-1)+1, 2^m+1),
  * p1(u) = 2^m + u - 2^(m-1) - 1: the order in which a decimation-in-frequency
- * column transform leaves the spectrum.  Entries u >= Py/2 + 1 (padding up
+ * column transform leaves the spectrum; plans whose columns run the
+ * 512-point radix-8 kernel (Py = 512, fused) hold entry u at ky(u) = u
+ * instead.  Entries u >= Py/2 + 1 (padding up
  * to QyS, a multiple of 16 bytes) are zero.  bytes is the size of out.
  * Asynchronous on stream.
  */

@@ -161,7 +161,7 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
             }
             if ((e = launch_extract_tensor(planes, p0, np, npairs, p->log2Px, p->log2Py, p->QyS,
                                            dst, p->precision == DEMAG_PREC_FP64, st,
-                                           layer < 0 ? p->umajor : 0)) !=
+                                           layer < 0 ? p->umajor : 0, p->natural)) !=
                 cudaSuccess) {
                 rc = cuda_fail(e, "tensor extraction kernel");
                 break;
@@ -276,6 +276,7 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
         p->contract_mode = 2;
     } else {
         p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
+        p->natural = !p->split && cols512_supported(p->log2Py, L, fp64) ? 1 : 0;
         if (p->split && !split_supported(L, max_batch, fp64)) {
             delete p;
             return fail(DEMAG_EUNSUPPORTED, "layer count x batch above the contraction kernels' limits");
@@ -373,6 +374,7 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.spec2 = plan->d_spec2;
     a.split = plan->split;
     a.contract_mode = plan->contract_mode;
+    a.natural = plan->natural;
     a.Ms = Ms;
     return a;
 }
@@ -446,6 +448,11 @@ demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     }
     if (path == 3 || path == 4)
         return fail(DEMAG_EUNSUPPORTED, "paths 3 and 4 need a DEMAG_PREC_SPLIT_TF32 plan");
+    if (plan->natural) {
+        if (path != 0 && path != 1 && path != 5)
+            return fail(DEMAG_EUNSUPPORTED, "plans on the 512-point fused kernel run path 5 only");
+        return DEMAG_OK;
+    }
     if (path == 0) path = plan->L > fused_max_layers(fp64, plan->log2Py) ? 2 : 1;
     if (path == 1) {
         if (plan->L > fused_max_layers(fp64, plan->log2Py))
@@ -538,7 +545,8 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     out[6] = plan->max_batch;
     out[7] = plan->npairs;
     out[8] = plan->QyS;
-    out[9] = plan->umajor ? (plan->contract_mode == 2 ? 4 : 3) : (plan->split ? 2 : 1);
+    out[9] = plan->umajor ? (plan->contract_mode == 2 ? 4 : 3)
+                          : (plan->split ? 2 : (plan->natural ? 5 : 1));
     return DEMAG_OK;
 }
 

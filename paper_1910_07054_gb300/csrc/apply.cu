@@ -335,21 +335,31 @@ static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t
                              (int)smem_rows);
     if (e != cudaSuccess) return e;
     dim3 grid_rows(chunks, planes);
+    const bool rows512 = a.log2Px == 9;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    k_rows_forward<T><<<grid_rows, kRowThreads, smem_rows, st>>>(m, (C *)a.spec, a.nx, a.ny, a.log2Px,
-                                                                 npair, (const C *)a.twx, a.log2twx,
-                                                                 (const T *)a.in_scale, a.L);
-    e = cudaGetLastError();
+    if (rows512)
+        e = launch_rows512<T>(a, m, H, true, st);
+    else {
+        k_rows_forward<T><<<grid_rows, kRowThreads, smem_rows, st>>>(m, (C *)a.spec, a.nx, a.ny, a.log2Px,
+                                                                     npair, (const C *)a.twx, a.log2twx,
+                                                                     (const T *)a.in_scale, a.L);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    e = a.split ? launch_split_columns(a, sizeof(T) == 8, st) : launch_fused<T>(a, st);
+    e = a.split ? launch_split_columns(a, sizeof(T) == 8, st)
+                : (a.natural ? launch_cols512<T>(a, st) : launch_fused<T>(a, st));
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-    k_rows_inverse<T><<<grid_rows, kRowThreads, smem_rows, st>>>((const C *)a.spec, H, a.nx, a.ny,
-                                                                 a.log2Px, npair, (const C *)a.twx,
-                                                                 a.log2twx, (T)(-a.Ms),
-                                                                 (const T *)a.out_scale, a.L);
-    e = cudaGetLastError();
+    if (rows512)
+        e = launch_rows512<T>(a, m, H, false, st);
+    else {
+        k_rows_inverse<T><<<grid_rows, kRowThreads, smem_rows, st>>>((const C *)a.spec, H, a.nx, a.ny,
+                                                                     a.log2Px, npair, (const C *)a.twx,
+                                                                     a.log2twx, (T)(-a.Ms),
+                                                                     (const T *)a.out_scale, a.L);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
     return cudaSuccess;

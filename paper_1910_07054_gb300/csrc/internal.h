@@ -63,7 +63,7 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
 // (umajor = 1, float only).
 cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs,
                                   int log2Px, int log2Py, int QyS, void *tensor, bool fp64,
-                                  cudaStream_t st, int umajor = 0);
+                                  cudaStream_t st, int umajor = 0, int natural = 0);
 
 // ---- apply ---------------------------------------------------------------
 struct ApplyArgs {
@@ -81,6 +81,7 @@ struct ApplyArgs {
     int full_pairs = 0;   // 1: tensor holds all L*L pairs (no reciprocity)
     int contract_mode = 0;  // split path: 0 per-item kernel, 1 dense products on
                             // FP32 cores, 2 dense products on tensor cores (3xTF32)
+    int natural = 0;      // 512-point column kernel, tensor in natural folded-ky order
     cudaEvent_t *inner_ev = nullptr;  // split path, optional [4]: before and after its 3 kernels
     const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
@@ -91,6 +92,13 @@ struct ApplyArgs {
 size_t gemm_smem_bytes(int L, int B);
 bool gemm_supported(int L, int B);
 cudaError_t launch_contract_gemm(const ApplyArgs &a, bool tensor_cores, cudaStream_t st);
+
+// 512-point transforms with the radix-8 engine (apply512.cu).
+bool cols512_supported(int log2Py, int L, bool fp64);
+template <typename T>
+cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forward, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cols512(const ApplyArgs &a, cudaStream_t st);
 
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);
@@ -119,6 +127,7 @@ struct demag_plan {
     int split = 0;                // 1: split path
     int contract_mode = 0;        // split path contraction (see ApplyArgs)
     int umajor = 0;               // tensor layout [Kx][Qy][npairs][6] (split-TF32 plans)
+    int natural = 0;              // fused 512-point column kernel, natural folded-ky tensor
     void *d_tscale = nullptr;     // [2L]: t_l, then 1 / t_l (plan real type)
     void *d_dtensor = nullptr;    // d N / d t_dlayer, all L*L pairs, [Kx][L*L][6][QyS]
     int dlayer = -1;              // layer of d_dtensor (-1: none)

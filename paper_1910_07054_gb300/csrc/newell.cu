@@ -737,7 +737,8 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
 // FFT(N_yz) = i b.
 template <typename T>
 __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, int npairs,
-                          int log2Px, int log2Py, int QyS, T *__restrict__ tensor, int umajor) {
+                          int log2Px, int log2Py, int QyS, T *__restrict__ tensor, int umajor,
+                          int natural) {
     const int Px = 1 << log2Px, Py = 1 << log2Py;
     const int Kx = Px / 2 + 1, Qy = Py / 2 + 1;
     const long long total = (long long)np * Kx * Qy;
@@ -746,7 +747,7 @@ __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, in
     const int u = (int)(idx % Qy);
     const int kx = (int)((idx / Qy) % Kx);
     const int P = (int)(idx / ((long long)Qy * Kx));
-    const int kq = u_kyq(u, log2Py);
+    const int kq = natural ? u : u_kyq(u, log2Py);
     const double2 *base = planes + (size_t)P * 3 * Px * Py + (size_t)kq * Px + kx;
     const double2 A = base[0], Bp = base[(size_t)Px * Py], C = base[(size_t)2 * Px * Py];
     const double sc = 1.0 / ((double)Px * (double)Py);
@@ -763,15 +764,15 @@ __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, in
 
 cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs, int log2Px,
                                   int log2Py, int QyS, void *tensor, bool fp64, cudaStream_t st,
-                                  int umajor) {
+                                  int umajor, int natural) {
     const long long total = (long long)np * ((1 << log2Px) / 2 + 1) * ((1 << log2Py) / 2 + 1);
     const unsigned grid = (unsigned)((total + 255) / 256);
     if (fp64)
         k_extract<double><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
-                                                (double *)tensor, umajor);
+                                                (double *)tensor, umajor, natural);
     else
         k_extract<float><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
-                                               (float *)tensor, umajor);
+                                               (float *)tensor, umajor, natural);
     return cudaGetLastError();
 }
 

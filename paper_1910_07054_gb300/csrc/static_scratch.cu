@@ -138,6 +138,7 @@ extern "C" demag_status demag_apply_static(const void *tensor, const double *thi
     a.log2Py = log2Py;
     a.npairs = L * (L + 1) / 2;
     a.QyS = tensor_row(log2Py, fp64);
+    a.natural = cols512_supported(log2Py, L, fp64) ? 1 : 0;
     a.tensor = tensor;
     a.ratio = b + spec + twx + twy;
     a.twx = b + spec;

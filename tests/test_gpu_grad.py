@@ -204,3 +204,34 @@ def test_autograd_function_routes_both_gradients():
     assert torch.allclose(m.grad, gm, rtol=0, atol=1e-12 * gm.abs().max().item())
     assert t.grad[1].item() == pytest.approx(g1, rel=1e-12)
     assert t.grad[0].item() == 0.0 and t.grad[2].item() == 0.0
+
+
+def test_adjoint_on_512_point_path():
+    """The radix-8 512-point kernels carry the adjoint's layer scales
+    (float64, 200 x 140 grid: 512-point rows and columns)."""
+    nx, ny, th = 200, 140, (1.0, 0.5, 2.0)
+    g = inputs.random_unit_vectors((1, len(th), ny, nx), seed=19)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP64)
+    assert plan.info["path"] == 5
+    gm = _adjoint(plan, g, 2.0)[0]
+    plan.close()
+    K = reading_kernels(nx, ny, 2.0, 2.0, th)
+    KT = np.transpose(K[:, :, :, ::-1, ::-1], (1, 0, 2, 3, 4))
+    assert rel_l2(gm, odm.hybrid(KT, g[0], 2.0)) < 1e-11
+
+
+@pytest.mark.parametrize("nx,ny", [(200, 3), (3, 140)])
+def test_dthickness_on_512_point_transforms(nx, ny):
+    """The derivative tensor's full pair set through the 512-point row
+    kernels (nx = 200) and the 512-point fused columns (ny = 140)."""
+    th = np.array([1.0, 2.0])
+    m = inputs.random_unit_vectors((1, len(th), ny, nx), seed=23)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, tuple(th), precision=dm.PREC_FP64)
+    assert plan.info["path"] == (5 if ny == 140 else 1)
+    mt = torch.tensor(m, dtype=torch.float64, device="cuda")
+    dH = torch.empty_like(mt)
+    dm.demag_apply_dthickness(plan.handle, mt, 2.0, dH, 1, info=plan.info)
+    torch.cuda.synchronize()
+    plan.close()
+    ref = odm.hybrid(onw.layer_dkernels(nx, ny, 2.0, 2.0, th, 1), m[0], 2.0)
+    assert rel_l2(dH[0].cpu().numpy(), ref) < 1e-9

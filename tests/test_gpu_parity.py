@@ -84,9 +84,12 @@ def test_tensor_points_match_oracle():
     assert np.allclose(N[len(g) - 5, :3], 1.0 / 3.0, atol=1e-15)
 
 
-def _stored_ky(Py):
+def _stored_ky(Py, path=1):
     """y-frequency held by each stored entry u (the documented order of
-    demag_plan_tensor: bit-reversed positions, one partner of each mirror pair)."""
+    demag_plan_tensor: bit-reversed positions, one partner of each mirror pair;
+    natural order on the 512-point path 5)."""
+    if path == 5:
+        return np.arange(Py // 2 + 1)
     n = Py.bit_length() - 1
     out = []
     for u in range(Py // 2 + 1):
@@ -101,7 +104,7 @@ def _stored_ky(Py):
 
 
 @pytest.mark.parametrize("nx,ny,th", [(7, 5, (1.0, 0.5, 2.0)), (4, 9, (0.8,)), (12, 3, (0.6, 3.0)),
-                                      (16, 16, (1.0, 2.0))])
+                                      (16, 16, (1.0, 2.0)), (200, 140, (1.0, 2.0))])
 def test_plan_tensor_matches_oracle_spectrum(nx, ny, th):
     """The stored Fourier tensor equals the oracle's kernels placed on the same
     padded grid and transformed by numpy's FFT (quadrant, divided by Px Py),
@@ -116,7 +119,9 @@ def test_plan_tensor_matches_oracle_spectrum(nx, ny, th):
     T = out.cpu().numpy().reshape(Kx, npairs, 6, QyS)
     plan.close()
     assert np.all(T[..., Qy:] == 0.0)
-    ky_of_u = _stored_ky(Py)
+    ky_of_u = _stored_ky(Py, info["path"])
+    if nx == 200:
+        assert info["path"] == 5
     assert sorted(ky_of_u.tolist()) == list(range(Qy))
     K = reading_kernels(nx, ny, 2.0, 2.0, tuple(th))
     pairs = [(i, j) for i in range(L) for j in range(i, L)]
@@ -149,7 +154,11 @@ def test_plain32_fp64_matches_direct_sum():
 
 
 RAGGED = [(7, 5, (1.0, 0.5, 2.0)), (1, 1, (2.0,)), (33, 17, (0.9, 1.3, 0.4, 2.2)), (16, 1, (1.0, 1.0)),
-          (3, 40, (0.7,)), (20, 20, (0.5, 1.5, 0.5, 2.5, 1.0, 0.8, 3.0, 1.1))]
+          (3, 40, (0.7,)), (20, 20, (0.5, 1.5, 0.5, 2.5, 1.0, 0.8, 3.0, 1.1)),
+          # 512-point transforms (radix-8 kernels), ragged rows and columns
+          (200, 140, (1.0, 0.5, 2.0)), (129, 256, (0.8, 1.7)), (256, 131, (1.2,)),
+          # 512-point columns under short rows, and 512-point rows over short columns
+          (5, 200, (1.0, 0.6)), (200, 6, (0.9, 2.0))]
 
 
 @pytest.mark.parametrize("nx,ny,th", RAGGED)
