@@ -378,8 +378,10 @@ def run_ours(args):
     tensor = Kx * npairs * 6 * Qy * 4
     stage_bytes = [field + spec, 2 * spec + tensor, spec + field]
     r8 = "8" if info["Px"] == 512 else ""
-    names = ["k_rows_forward" + r8, "k_columns_fused" + ("8" if info["path"] == 5 else ""),
-             "k_rows_inverse" + r8]
+    col = "k_columns_fused"
+    if info["path"] == 5:
+        col = "k_columns_ring8" if L <= 8 else "k_columns_fused8"
+    names = ["k_rows_forward" + r8, col, "k_rows_inverse" + r8]
     dom = int(np.argmax(stage))
     peak, peak_kind = measured_hbm_peak()
     achieved = stage_bytes[dom] / (stage[dom] * 1e-3) / 1e9

@@ -70,6 +70,21 @@ const char *demag_status_string(demag_status status);
 const char *demag_last_error(void);
 
 /*
+ * demag_wait_timeouts - count of bounded device waits that gave up.
+ *
+ * Not a step of the paper's method: a health check of the kernels that stream
+ * the plan tensor through shared memory with asynchronous bulk copies.  Each
+ * of their waits on a copy is bounded (about one second); a wait that runs out
+ * is counted on the device and the kernel completes without hanging, but the
+ * field it wrote is then invalid.  This call synchronises the current device,
+ * stores the count accumulated since the previous call in *count and clears
+ * it.  Returns DEMAG_EINVAL for a NULL count, DEMAG_ECUDA if the counter
+ * cannot be read.  A non-zero count means some apply since the previous call
+ * produced an invalid field.
+ */
+demag_status demag_wait_timeouts(unsigned long long *count);
+
+/*
  * demag_plan_create - build the Fourier-space layer tensor of a layer stack.
  *
  * Sec. 2 (generalized Newell tensor) and Sec. 3 (Eq. FFT_v2).  For every pair

@@ -87,6 +87,8 @@ def lib():
     L.demag_layer_mean.restype = i
     L.demag_destroy.argtypes = [vp]
     L.demag_destroy.restype = i
+    L.demag_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+    L.demag_wait_timeouts.restype = i
     _lib = L
     return L
 
@@ -316,6 +318,13 @@ def demag_layer_mean(H, precision, layer, out, stream=None):
     _check(lib().demag_layer_mean(_ptr(H), int(precision), int(B), int(L), int(ny), int(nx), int(layer),
                                   _ptr(out), _stream(stream)), "demag_layer_mean")
     return out
+
+
+def demag_wait_timeouts():
+    """Bounded device waits that gave up since the previous call (synchronises the device)."""
+    n = ctypes.c_ulonglong(0)
+    _check(lib().demag_wait_timeouts(ctypes.byref(n)), "demag_wait_timeouts")
+    return int(n.value)
 
 
 def demag_destroy(plan):

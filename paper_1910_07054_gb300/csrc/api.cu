@@ -224,6 +224,16 @@ const char *demag_status_string(demag_status s) {
 
 const char *demag_last_error(void) { return g_last_error.c_str(); }
 
+demag_status demag_wait_timeouts(unsigned long long *count) {
+    if (!count) return fail(DEMAG_EINVAL, "count is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    const unsigned n = take_wait_timeouts();
+    if (n == ~0u) return fail(DEMAG_ECUDA, "cannot read the wait-timeout counter");
+    *count = n;
+    return DEMAG_OK;
+}
+
 demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, double dy,
                                const double *thickness, int L, int precision, int max_batch,
                                void *stream) {

@@ -13,8 +13,12 @@
 // Shared memory holds columns of 512 values with one padding slot per 8
 // (index p + p / 8), which makes the radix-8 stores of the first pass
 // conflict-free.
+#include <algorithm>
+#include <cstdint>
+
 #include "fft8.cuh"
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace demag {
 
@@ -208,6 +212,30 @@ __device__ __forceinline__ void block_apply8(C &ox, C &oy, C &oz, T kxx, T kyy, 
     oz.y += kxz * mx.x + kyz * my.x + kzz * mz.y;
 }
 
+// Same product as block_apply8, as one fused multiply-add chain per output.
+template <typename C, typename T>
+__device__ __forceinline__ void block_fma8(C &ox, C &oy, C &oz, T kxx, T kyy, T kzz, T kxy, T kxz, T kyz, C mx,
+                                           C my, C mz) {
+    ox.x = fma(kxx, mx.x, ox.x);
+    ox.x = fma(kxy, my.x, ox.x);
+    ox.x = fma(-kxz, mz.y, ox.x);
+    ox.y = fma(kxx, mx.y, ox.y);
+    ox.y = fma(kxy, my.y, ox.y);
+    ox.y = fma(kxz, mz.x, ox.y);
+    oy.x = fma(kxy, mx.x, oy.x);
+    oy.x = fma(kyy, my.x, oy.x);
+    oy.x = fma(-kyz, mz.y, oy.x);
+    oy.y = fma(kxy, mx.y, oy.y);
+    oy.y = fma(kyy, my.y, oy.y);
+    oy.y = fma(kyz, mz.x, oy.y);
+    oz.x = fma(-kxz, mx.y, oz.x);
+    oz.x = fma(-kyz, my.y, oz.x);
+    oz.x = fma(kzz, mz.x, oz.x);
+    oz.y = fma(kxz, mx.x, oz.y);
+    oz.y = fma(kyz, my.x, oz.y);
+    oz.y = fma(kzz, mz.y, oz.y);
+}
+
 // Prefetch of [p, p + bytes) into L2 by bulk requests (p, bytes multiples of 16).
 __device__ __forceinline__ void prefetch_l2_8(const void *p, size_t bytes) {
     const char *c = static_cast<const char *>(p);
@@ -351,6 +379,333 @@ __global__ void __launch_bounds__(256, 2) k_columns_fused8(typename cpx_of<T>::t
     }
 }
 
+// ---------------------------------------------------------------------------
+// Float columns for L <= 8 layers: the tensor streamed through shared memory.
+//
+// One block of 512 threads per (kx, state).  The 3L columns are transformed by
+// eight 64-thread groups; in the contraction thread p owns the y-frequency
+// position p (0 <= p < 512) in every column, so it reads and overwrites only
+// its own entries and holds the field of all L target layers in registers.
+// Each stored pair (i <= j) of the plan tensor then serves both directions,
+// N(i<-j) m_j into layer i and, by reciprocity, (t_i / t_j) N'(j<-i) m_i into
+// layer j (xz and yz change sign), so the tensor of one kx (6 reals per pair
+// and folded frequency) is read exactly once.  It arrives in a ring of
+// shared-memory stages, one pair per stage, by bulk copies that thread 0
+// starts at block entry (overlapping the forward transforms) and re-arms as
+// the stages drain.  Positions p > 256 take the stored entry q = 512 - p with
+// xy and yz negated, done by negating m_y before and H_y after the sums.
+template <int L>
+struct Ring8 {
+    static constexpr int kCols = 3 * L;
+    static constexpr int kColsPerGroup = (kCols + 7) / 8;
+    static constexpr int kPairs = L * (L + 1) / 2;
+    static constexpr int kStages = kPairs < 16 ? kPairs : 16;
+};
+
+static __device__ unsigned g_wait_timeouts8;
+
+// Twiddles of passes 2 (W_64^{r k}, k = j mod 8) and 3 (W_512^{r j}), r = 1..7.
+template <bool INV, typename C>
+__device__ __forceinline__ void load_twiddles8(C (&w2)[7], C (&w3)[7], const C *__restrict__ tw, int j) {
+    const int k = j & 7;
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+        w2[r - 1] = tw512<INV>(tw, 8 * r * k);
+        w3[r - 1] = tw512<INV>(tw, r * j);
+    }
+}
+
+// Pass 2 of the group's columns, shared memory to shared memory.
+template <bool INV, int CPG, typename C>
+__device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, int bj, int b2, const C (&w2)[7],
+                                            C (&v)[CPG][8]) {
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < ncol) {
+            const C *col = cols + c * kCol8 + bj;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
+        }
+    }
+    group_sync(group);
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < ncol) {
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w2[r - 1]);
+            dft8<INV>(v[u]);
+            C *col = cols + c * kCol8 + b2;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) col[9 * r] = v[u][r];
+        }
+    }
+    group_sync(group);
+}
+
+template <int L>
+__global__ void __launch_bounds__(512, 1) k_columns_ring8(float2 *__restrict__ spec,
+                                                        const float *__restrict__ tensor,
+                                                        const float *__restrict__ ratio, int Kx, int ny,
+                                                        int QyS, const float2 *__restrict__ tw) {
+    using C = float2;
+    using T = float;
+    using R = Ring8<L>;
+    constexpr int NC = R::kCols, CPG = R::kColsPerGroup, NP = R::kPairs, NS = R::kStages;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *cols = reinterpret_cast<C *>(smem_raw);                                      // NC x kCol8
+    T *ring = reinterpret_cast<T *>(smem_raw + (size_t)NC * kCol8 * sizeof(C));  // NS x 6 x QyS
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    __shared__ T s_ratio[L * L];
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, group = tid >> 6, j = tid & 63, lane = tid & 31;
+    const int kx = blockIdx.x;
+    const unsigned stage_elems = 6u * (unsigned)QyS, stage_bytes = stage_elems * (unsigned)sizeof(T);
+    const T *tk = tensor + (size_t)kx * NP * stage_elems;
+    C *sp = spec + ((size_t)blockIdx.y * NC * Kx + kx) * ny;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 16);
+        }
+        mbar_init_fence();
+        s_abort = 0;
+    }
+    if (tid < L * L) s_ratio[tid] = ratio[tid];
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int P = 0; P < NS; ++P) {
+            mbar_arrive_expect_tx(&full[P], stage_bytes);
+            bulk_copy_g2s(ring + P * stage_elems, tk + (size_t)P * stage_elems, stage_bytes, &full[P]);
+        }
+    }
+
+    // forward transforms: pass 1 from global memory (all loads issued first)
+    const int bj = j + (j >> 3), b2 = (j >> 3) * 72 + (j & 7), b1 = 9 * j;
+    C w2[7], w3[7];
+    load_twiddles8<false>(w2, w3, tw, j);
+    C v[CPG][8];
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int y = j + 64 * r;
+            v[u][r] = (c < NC && y < ny) ? sp[(size_t)c * Kx * ny + y] : C{0, 0};
+        }
+#pragma unroll
+        for (int r = 4; r < 8; ++r) v[u][r] = C{0, 0};
+    }
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < NC) {
+            dft8<false>(v[u]);
+            C *col = cols + c * kCol8 + b1;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) col[r] = v[u][r];
+        }
+    }
+    group_sync(group);
+    ring8_pass2<false, CPG>(cols, group, NC, bj, b2, w2, v);
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < NC) {
+            C *col = cols + c * kCol8 + bj;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w3[r - 1]);
+            dft8<false>(v[u]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) col[72 * r] = v[u][r];
+        }
+    }
+    __syncthreads();
+
+    // contraction at position p = tid; pair P + 1's tensor entry and source m
+    // are loaded while pair P is applied, and m_i of the pair row stays in
+    // registers (the row opens with the diagonal pair (i, i))
+    {
+        const int p = tid;
+        const int q = p <= kN8 / 2 ? p : kN8 - p;
+        const bool mir = p > kN8 / 2;
+        C *mp = cols + p + (p >> 3);
+        if (mir) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const C t = mp[(3 * l + 1) * kCol8];
+                mp[(3 * l + 1) * kCol8] = C{-t.x, -t.y};
+            }
+        }
+        C acc[L][3];
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[l][c] = C{0, 0};
+        T kn[6], rn = (T)1;
+        C mn[3];
+        if (!s_abort && !mbar_wait(&full[0], 0, &g_wait_timeouts8)) s_abort = 1;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) kn[c] = ring[c * QyS + q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mn[c] = mp[c * kCol8];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            C mi[3];
+#pragma unroll
+            for (int jj = i; jj < L; ++jj) {
+                const int P = i * L - (i * (i - 1)) / 2 + (jj - i);
+                T kc[6];
+                C mc[3];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) kc[c] = kn[c];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) mc[c] = mn[c];
+                if (jj == i) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) mi[c] = mc[c];
+                }
+                const T rr = rn;  // t_i / t_jj for this pair
+                if (P >= 1 && P - 1 + NS < NP && tid == 0) {
+                    // re-arm the stage of pair P - 1 with pair P - 1 + NS
+                    const int s1 = (P - 1) % NS;
+                    if (!s_abort && !mbar_wait(&empty[s1], ((P - 1) / NS) & 1, &g_wait_timeouts8))
+                        s_abort = 1;
+                    mbar_arrive_expect_tx(&full[s1], stage_bytes);
+                    bulk_copy_g2s(ring + s1 * stage_elems, tk + (size_t)(P - 1 + NS) * stage_elems, stage_bytes,
+                                  &full[s1]);
+                }
+                if (P + 1 < NP) {
+                    // the next pair is (i, jj + 1) or (i + 1, i + 1)
+                    const int s2 = (P + 1) % NS;
+                    const int jn = jj + 1 < L ? jj + 1 : i + 1;
+                    if (!*(volatile int *)&s_abort && !mbar_wait(&full[s2], ((P + 1) / NS) & 1, &g_wait_timeouts8))
+                        s_abort = 1;
+                    const T *kp = ring + s2 * stage_elems + q;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) kn[c] = kp[c * QyS];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) mn[c] = mp[(3 * jn + c) * kCol8];
+                    rn = jj + 1 < L ? s_ratio[(jj + 1) * L + i] : (T)1;
+                }
+                block_fma8(acc[i][0], acc[i][1], acc[i][2], kc[0], kc[1], kc[2], kc[3], kc[4], kc[5], mc[0], mc[1],
+                           mc[2]);
+                if (jj != i)
+                    block_fma8(acc[jj][0], acc[jj][1], acc[jj][2], rr * kc[0], rr * kc[1], rr * kc[2],
+                               rr * kc[3], -rr * kc[4], -rr * kc[5], mi[0], mi[1], mi[2]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[P % NS]);
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            C *o = mp + 3 * l * kCol8;
+            o[0] = acc[l][0];
+            o[kCol8] = mir ? C{-acc[l][1].x, -acc[l][1].y} : acc[l][1];
+            o[2 * kCol8] = acc[l][2];
+        }
+    }
+    __syncthreads();
+    if (s_abort && tid == 0) {
+        // a wait gave up: let the copies still in flight land (bounded) before exit
+#pragma unroll
+        for (int s = 0; s < NS; ++s) mbar_wait(&full[s], ((NP - 1 - s) / NS) & 1, &g_wait_timeouts8);
+    }
+
+    // inverse transforms: pass 1 in shared memory, pass 3 to global memory
+    load_twiddles8<true>(w2, w3, tw, j);
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < NC) {
+            const C *col = cols + c * kCol8 + bj;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
+        }
+    }
+    group_sync(group);
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < NC) {
+            dft8<true>(v[u]);
+            C *col = cols + c * kCol8 + b1;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) col[r] = v[u][r];
+        }
+    }
+    group_sync(group);
+    ring8_pass2<true, CPG>(cols, group, NC, bj, b2, w2, v);
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < NC) {
+            const C *col = cols + c * kCol8 + bj;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w3[r - 1]);
+            dft8<true>(v[u]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int y = j + 64 * r;
+                if (y < ny) sp[(size_t)c * Kx * ny + y] = v[u][r];
+            }
+        }
+    }
+}
+
+template <int L>
+static cudaError_t launch_ring8(const ApplyArgs &a, cudaStream_t st) {
+    using R = Ring8<L>;
+    const size_t smem = (size_t)R::kCols * kCol8 * sizeof(float2) + (size_t)R::kStages * 6 * a.QyS * sizeof(float);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_columns_ring8<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    const int Kx = (1 << a.log2Px) / 2 + 1;
+    k_columns_ring8<L><<<dim3(Kx, a.B), 512, smem, st>>>((float2 *)a.spec, (const float *)a.tensor,
+                                                         (const float *)a.ratio, Kx, a.ny, a.QyS,
+                                                         (const float2 *)a.twy);
+    return cudaGetLastError();
+}
+
+// The streamed kernel takes float plans with L <= 8, the pair-symmetric
+// tensor, a 16-byte stage size and a 16-byte aligned tensor.
+static bool ring8_supported(const ApplyArgs &a, bool fp64) {
+    if (fp64 || a.full_pairs || a.L < 1 || a.L > 8 || a.QyS % 4 != 0) return false;
+    if ((reinterpret_cast<uintptr_t>(a.tensor) & 15) != 0) return false;
+    const size_t smem = (size_t)3 * a.L * kCol8 * sizeof(float2) +
+                        (size_t)std::min(a.L * (a.L + 1) / 2, 16) * 6 * a.QyS * sizeof(float);
+    return smem <= 227 * 1024;
+}
+
+static cudaError_t launch_ring8_any(const ApplyArgs &a, cudaStream_t st) {
+    switch (a.L) {
+    case 1: return launch_ring8<1>(a, st);
+    case 2: return launch_ring8<2>(a, st);
+    case 3: return launch_ring8<3>(a, st);
+    case 4: return launch_ring8<4>(a, st);
+    case 5: return launch_ring8<5>(a, st);
+    case 6: return launch_ring8<6>(a, st);
+    case 7: return launch_ring8<7>(a, st);
+    default: return launch_ring8<8>(a, st);
+    }
+}
+
+unsigned take_wait_timeouts() {
+    unsigned n = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&n, g_wait_timeouts8, sizeof(n)) != cudaSuccess) return ~0u;
+    if (n != 0) cudaMemcpyToSymbol(g_wait_timeouts8, &zero, sizeof(zero));
+    return n;
+}
+
 bool cols512_supported(int log2Py, int L, bool fp64) {
     const size_t elem = fp64 ? sizeof(double2) : sizeof(float2);
     return log2Py == 9 && (size_t)3 * L * kCol8 * elem <= 220 * 1024;
@@ -382,6 +737,7 @@ cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forw
 template <typename T>
 cudaError_t launch_cols512(const ApplyArgs &a, cudaStream_t st) {
     using C = typename cpx_of<T>::type;
+    if (ring8_supported(a, sizeof(T) == 8)) return launch_ring8_any(a, st);
     const size_t smem = (size_t)3 * a.L * kCol8 * sizeof(C);
     int TU = 1;
     while (2 * TU * a.L <= 256) TU *= 2;

@@ -99,6 +99,9 @@ template <typename T>
 cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forward, cudaStream_t st);
 template <typename T>
 cudaError_t launch_cols512(const ApplyArgs &a, cudaStream_t st);
+// Bounded waits of the streamed column kernel that gave up since the last
+// call (the count is cleared); ~0u if the counter could not be read.
+unsigned take_wait_timeouts();
 
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);

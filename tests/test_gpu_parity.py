@@ -171,6 +171,22 @@ def test_ragged_grids_match_oracle_hybrid(nx, ny, th, prec):
     assert rel_l2(H, H_ref) < (TOL64 if prec == dm.PREC_FP64 else TOL32)
 
 
+@pytest.mark.parametrize("L", range(1, 9))
+def test_streamed_columns_every_layer_count(L):
+    """Float plans with 512-point columns and L <= 8 take the kernel that streams
+    the tensor through shared memory (every unrolled pair count, ragged grid,
+    batch of two states); no bounded wait may give up."""
+    rng = np.random.default_rng(40 + L)
+    th = tuple(np.round(rng.uniform(0.4, 3.0, L), 3))
+    nx, ny = 150, 131
+    m = inputs.random_unit_vectors((2, L, ny, nx), seed=L)
+    K = reading_kernels(nx, ny, 2.0, 1.5, th)
+    H = _gpu_field(nx, ny, 2.0, 1.5, th, m, 1.0, dm.PREC_FP32, max_batch=2)
+    assert dm.demag_wait_timeouts() == 0
+    for b in range(2):
+        assert rel_l2(H[b], odm.hybrid(K, m[b], 1.0)) < TOL32
+
+
 def test_sixteen_layers_fp32():
     th = tuple(np.round(np.linspace(0.5, 3.0, 16), 3))
     nx = ny = 24
