@@ -58,6 +58,15 @@ __device__ __forceinline__ void passes23(C *col, int j, const C *__restrict__ tw
     }
 }
 
+// Prefetch of [p, p + bytes) into L2 by bulk requests (p, bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2_8(const void *p, size_t bytes) {
+    const char *c = static_cast<const char *>(p);
+    for (size_t off = 0; off < bytes; off += 65536) {
+        const unsigned n = (unsigned)((bytes - off) < 65536 ? (bytes - off) : 65536);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
                                                       typename cpx_of<T>::type *__restrict__ spec,
@@ -236,15 +245,6 @@ __device__ __forceinline__ void block_fma8(C &ox, C &oy, C &oz, T kxx, T kyy, T 
     oz.y = fma(kzz, mz.y, oz.y);
 }
 
-// Prefetch of [p, p + bytes) into L2 by bulk requests (p, bytes multiples of 16).
-__device__ __forceinline__ void prefetch_l2_8(const void *p, size_t bytes) {
-    const char *c = static_cast<const char *>(p);
-    for (size_t off = 0; off < bytes; off += 65536) {
-        const unsigned n = (unsigned)((bytes - off) < 65536 ? (bytes - off) : 65536);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
-    }
-}
-
 template <typename T, bool FULL>
 __global__ void __launch_bounds__(256, 2) k_columns_fused8(typename cpx_of<T>::type *__restrict__ spec,
                                                           const T *__restrict__ tensor,
@@ -394,13 +394,31 @@ __global__ void __launch_bounds__(256, 2) k_columns_fused8(typename cpx_of<T>::t
 // starts at block entry (overlapping the forward transforms) and re-arms as
 // the stages drain.  Positions p > 256 take the stored entry q = 512 - p with
 // xy and yz negated, done by negating m_y before and H_y after the sums.
+//
+// Columns are padded by one slot per 16 (index p + p / 16): the stride-1
+// accesses (j + 64 r), the first pass's stride-8 stores (8 j + r) and the
+// second pass's stores (64 (j / 8) + j mod 8 + 8 r) are then all free of bank
+// conflicts for 8-byte elements, with constant offsets from per-thread bases.
+// The pair loop runs over rows at run time and is unrolled only over the
+// source layer, which keeps the code small enough for the instruction cache.
+constexpr int kColR = kN8 + kN8 / 16;    // padded column length of the streamed kernel
+constexpr int kQyS8 = 260;               // stored frequencies per tensor row (257 padded to 16 B)
+constexpr int kStage8 = 6 * kQyS8;       // floats per pair stage
+constexpr int kRingBudget = 225 * 1024;  // dynamic shared memory of the streamed kernel
+
 template <int L>
 struct Ring8 {
     static constexpr int kCols = 3 * L;
     static constexpr int kColsPerGroup = (kCols + 7) / 8;
     static constexpr int kPairs = L * (L + 1) / 2;
-    static constexpr int kStages = kPairs < 16 ? kPairs : 16;
+    static constexpr int kFit = (kRingBudget - kCols * kColR * 8) / (kStage8 * 4);
+    static constexpr int kStages = kPairs < kFit ? kPairs : kFit;  // pair slots of the ring
+    static constexpr size_t kSmem = (size_t)kCols * kColR * 8 + (size_t)kStages * kStage8 * 4;
+    // first stored pair of row i (pairs (i, j >= i), row by row)
+    static __host__ __device__ constexpr int first(int i) { return i * L - (i * (i - 1)) / 2; }
 };
+
+__device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
 
 static __device__ unsigned g_wait_timeouts8;
 
@@ -415,17 +433,26 @@ __device__ __forceinline__ void load_twiddles8(C (&w2)[7], C (&w3)[7], const C *
     }
 }
 
+// Per-thread bases of the three access patterns (see the layout note above).
+struct Bases8 {
+    int b1;  // 8 j + r       -> b1 + r
+    int bj;  // j + 64 r      -> bj + 68 r
+    int b2;  // pass-2 store  -> b2 + 8 r + r / 2
+    __device__ explicit Bases8(int j)
+        : b1(8 * j + (j >> 1)), bj(j + (j >> 4)), b2(68 * (j >> 3) + (j & 7)) {}
+};
+
 // Pass 2 of the group's columns, shared memory to shared memory.
 template <bool INV, int CPG, typename C>
-__device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, int bj, int b2, const C (&w2)[7],
+__device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const Bases8 &bs, const C (&w2)[7],
                                             C (&v)[CPG][8]) {
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
         const int c = group + 8 * u;
         if (c < ncol) {
-            const C *col = cols + c * kCol8 + bj;
+            const C *col = cols + c * kColR + bs.bj;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
+            for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
         }
     }
     group_sync(group);
@@ -436,187 +463,213 @@ __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, int bj
 #pragma unroll
             for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w2[r - 1]);
             dft8<INV>(v[u]);
-            C *col = cols + c * kCol8 + b2;
+            C *col = cols + c * kColR + bs.b2;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) col[9 * r] = v[u][r];
+            for (int r = 0; r < 8; ++r) col[8 * r + (r >> 1)] = v[u][r];
         }
     }
     group_sync(group);
 }
 
+// Pass 3 in place (positions j + 64 r), result left in v.
+template <bool INV, int CPG, typename C>
+__device__ __forceinline__ void ring8_pass3(C *cols, int group, int ncol, const Bases8 &bs, const C (&w3)[7],
+                                            C (&v)[CPG][8], bool store) {
+#pragma unroll
+    for (int u = 0; u < CPG; ++u) {
+        const int c = group + 8 * u;
+        if (c < ncol) {
+            C *col = cols + c * kColR + bs.bj;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w3[r - 1]);
+            dft8<INV>(v[u]);
+            if (store) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) col[68 * r] = v[u][r];
+            }
+        }
+    }
+}
+
+// Thread 0: bulk copies of pairs [P, P_end) into their ring slots (pair P in
+// slot P mod NS), each completing on its row's barrier.  A row announces its
+// full byte count with its first pair, so its barrier completes only when all
+// of its pairs have landed, whichever copies brought them.  Runs of pairs of
+// one row with consecutive slots go in one copy.
 template <int L>
-__global__ void __launch_bounds__(512, 1) k_columns_ring8(float2 *__restrict__ spec,
+__device__ __forceinline__ void ring8_issue(int P, int P_end, float *ring, const float *tk, uint64_t *full_row) {
+    using R = Ring8<L>;
+    while (P < P_end) {
+        int k = 0;
+        while (R::first(k + 1) <= P) ++k;
+        if (P == R::first(k))
+            mbar_arrive_expect_tx(&full_row[k], (unsigned)((L - k) * kStage8 * sizeof(float)));
+        const int s = P % R::kStages;
+        int n = R::first(k + 1) - P;                  // rest of the row
+        if (n > P_end - P) n = P_end - P;             // not past the free slots
+        if (n > R::kStages - s) n = R::kStages - s;   // not past the last slot
+        bulk_copy_g2s(ring + s * kStage8, tk + (size_t)P * kStage8, (unsigned)(n * kStage8 * sizeof(float)),
+                      &full_row[k]);
+        P += n;
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ spec,
                                                         const float *__restrict__ tensor,
                                                         const float *__restrict__ ratio, int Kx, int ny,
-                                                        int QyS, const float2 *__restrict__ tw) {
+                                                        const float2 *__restrict__ tw) {
     using C = float2;
     using T = float;
     using R = Ring8<L>;
     constexpr int NC = R::kCols, CPG = R::kColsPerGroup, NP = R::kPairs, NS = R::kStages;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *cols = reinterpret_cast<C *>(smem_raw);                                      // NC x kCol8
-    T *ring = reinterpret_cast<T *>(smem_raw + (size_t)NC * kCol8 * sizeof(C));  // NS x 6 x QyS
-    __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    C *cols = reinterpret_cast<C *>(smem_raw);                                      // NC x kColR
+    T *ring = reinterpret_cast<T *>(smem_raw + (size_t)NC * kColR * sizeof(C));  // NS x kStage8
+    __shared__ __align__(8) uint64_t full_row[L], empty_row[L];
     __shared__ T s_ratio[L * L];
     __shared__ int s_abort;
     const int tid = threadIdx.x, group = tid >> 6, j = tid & 63, lane = tid & 31;
     const int kx = blockIdx.x;
-    const unsigned stage_elems = 6u * (unsigned)QyS, stage_bytes = stage_elems * (unsigned)sizeof(T);
-    const T *tk = tensor + (size_t)kx * NP * stage_elems;
+    const T *tk = tensor + (size_t)kx * NP * kStage8;
     C *sp = spec + ((size_t)blockIdx.y * NC * Kx + kx) * ny;
+    bool ok = true;  // false once one of this thread's waits gave up
 
     if (tid == 0) {
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 16);
+        for (int r = 0; r < L; ++r) {
+            mbar_init(&full_row[r], 1);
+            mbar_init(&empty_row[r], 16);
         }
         mbar_init_fence();
         s_abort = 0;
     }
     if (tid < L * L) s_ratio[tid] = ratio[tid];
     __syncthreads();
-    if (tid == 0) {
-#pragma unroll
-        for (int P = 0; P < NS; ++P) {
-            mbar_arrive_expect_tx(&full[P], stage_bytes);
-            bulk_copy_g2s(ring + P * stage_elems, tk + (size_t)P * stage_elems, stage_bytes, &full[P]);
-        }
-    }
+    // warp 16 only copies the tensor: a bulk copy can hold its issuing thread
+    // until the copy engine takes it, which must not stall a compute warp
+    const bool producer = tid >= 512;
+    if (producer && lane == 0) ring8_issue<L>(0, NS, ring, tk, full_row);
 
-    // forward transforms: pass 1 from global memory (all loads issued first)
-    const int bj = j + (j >> 3), b2 = (j >> 3) * 72 + (j & 7), b1 = 9 * j;
+    const Bases8 bs(j);
     C w2[7], w3[7];
-    load_twiddles8<false>(w2, w3, tw, j);
     C v[CPG][8];
+    if (!producer) {
+        // forward transforms: pass 1 from global memory (all loads issued first)
+        load_twiddles8<false>(w2, w3, tw, j);
 #pragma unroll
-    for (int u = 0; u < CPG; ++u) {
-        const int c = group + 8 * u;
+        for (int u = 0; u < CPG; ++u) {
+            const int c = group + 8 * u;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int y = j + 64 * r;
-            v[u][r] = (c < NC && y < ny) ? sp[(size_t)c * Kx * ny + y] : C{0, 0};
+            for (int r = 0; r < 4; ++r) {
+                const int y = j + 64 * r;
+                v[u][r] = (c < NC && y < ny) ? sp[(size_t)c * Kx * ny + y] : C{0, 0};
+            }
+#pragma unroll
+            for (int r = 4; r < 8; ++r) v[u][r] = C{0, 0};
         }
 #pragma unroll
-        for (int r = 4; r < 8; ++r) v[u][r] = C{0, 0};
-    }
+        for (int u = 0; u < CPG; ++u) {
+            const int c = group + 8 * u;
+            if (c < NC) {
+                dft8<false>(v[u]);
+                C *col = cols + c * kColR + bs.b1;
 #pragma unroll
-    for (int u = 0; u < CPG; ++u) {
-        const int c = group + 8 * u;
-        if (c < NC) {
-            dft8<false>(v[u]);
-            C *col = cols + c * kCol8 + b1;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) col[r] = v[u][r];
+                for (int r = 0; r < 8; ++r) col[r] = v[u][r];
+            }
         }
-    }
-    group_sync(group);
-    ring8_pass2<false, CPG>(cols, group, NC, bj, b2, w2, v);
-#pragma unroll
-    for (int u = 0; u < CPG; ++u) {
-        const int c = group + 8 * u;
-        if (c < NC) {
-            C *col = cols + c * kCol8 + bj;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
-#pragma unroll
-            for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w3[r - 1]);
-            dft8<false>(v[u]);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) col[72 * r] = v[u][r];
-        }
+        group_sync(group);
+        ring8_pass2<false, CPG>(cols, group, NC, bs, w2, v);
+        ring8_pass3<false, CPG>(cols, group, NC, bs, w3, v, true);
     }
     __syncthreads();
 
-    // contraction at position p = tid; pair P + 1's tensor entry and source m
-    // are loaded while pair P is applied, and m_i of the pair row stays in
-    // registers (the row opens with the diagonal pair (i, i))
-    {
+    // contraction at position p = tid: m of every layer and the field of every
+    // target in registers; pair rows i in order, each behind its copy barrier
+    if (producer) {
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 1; i < L; ++i) {
+                if (R::first(i - 1) + NS >= NP) break;
+                // row i - 1 released: its slots take the next pairs
+                if (ok && !mbar_wait(&empty_row[i - 1], 0, &g_wait_timeouts8)) ok = false;
+                const int hi = R::first(i) + NS < NP ? R::first(i) + NS : NP;
+                ring8_issue<L>(R::first(i - 1) + NS, hi, ring, tk, full_row);
+            }
+        }
+    } else {
         const int p = tid;
         const int q = p <= kN8 / 2 ? p : kN8 - p;
         const bool mir = p > kN8 / 2;
-        C *mp = cols + p + (p >> 3);
+        C *mp = cols + pad16(p);
         if (mir) {
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                const C t = mp[(3 * l + 1) * kCol8];
-                mp[(3 * l + 1) * kCol8] = C{-t.x, -t.y};
+                const C t = mp[(3 * l + 1) * kColR];
+                mp[(3 * l + 1) * kColR] = C{-t.x, -t.y};
             }
         }
-        C acc[L][3];
+        // m of layers >= KR stays in registers (m_j serves rows 0..j, so the
+        // upper layers are reused most); lower layers are read when used
+        constexpr int KR = L / 2;
+        C acc[L][3], m[L][3];
 #pragma unroll
         for (int l = 0; l < L; ++l)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[l][c] = C{0, 0};
-        T kn[6], rn = (T)1;
-        C mn[3];
-        if (!s_abort && !mbar_wait(&full[0], 0, &g_wait_timeouts8)) s_abort = 1;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) kn[c] = ring[c * QyS + q];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mn[c] = mp[c * kCol8];
+            for (int c = 0; c < 3; ++c) {
+                acc[l][c] = C{0, 0};
+                if (l >= KR) m[l][c] = mp[(3 * l + c) * kColR];
+            }
+        const T *rq = ring + q;
 #pragma unroll
         for (int i = 0; i < L; ++i) {
-            C mi[3];
+            if (ok && !mbar_wait(&full_row[i], 0, &g_wait_timeouts8)) ok = false;
+            // acc[i] so far holds the reciprocal terms with sources scaled by
+            // tau_j = t_j / t_0; dividing by tau_i gives sum_j (t_j / t_i) N' m_j
+            if (i > 0) {
+                const T inv_tau = s_ratio[i * L];  // t_0 / t_i
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[i][c] = C{inv_tau * acc[i][c].x, inv_tau * acc[i][c].y};
+            }
+            C mi[3];  // the row's reciprocal source, scaled by tau_i
 #pragma unroll
             for (int jj = i; jj < L; ++jj) {
-                const int P = i * L - (i * (i - 1)) / 2 + (jj - i);
-                T kc[6];
-                C mc[3];
+                const int P = R::first(i) + jj - i;
+                const T *kp = rq + (P % NS) * kStage8;
+                const T kxx = kp[0], kyy = kp[kQyS8], kzz = kp[2 * kQyS8];
+                const T kxy = kp[3 * kQyS8], kxz = kp[4 * kQyS8], kyz = kp[5 * kQyS8];
+                C mj[3];
 #pragma unroll
-                for (int c = 0; c < 6; ++c) kc[c] = kn[c];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) mc[c] = mn[c];
+                for (int c = 0; c < 3; ++c) mj[c] = jj >= KR ? m[jj][c] : mp[(3 * jj + c) * kColR];
+                block_fma8(acc[i][0], acc[i][1], acc[i][2], kxx, kyy, kzz, kxy, kxz, kyz, mj[0], mj[1], mj[2]);
                 if (jj == i) {
+                    // m_i is no longer a direct source: scale it for the reciprocal terms
+                    const T tau = s_ratio[i];  // t_i / t_0
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) mi[c] = mc[c];
+                    for (int c = 0; c < 3; ++c) mi[c] = C{tau * mj[c].x, tau * mj[c].y};
+                } else {
+                    block_fma8(acc[jj][0], acc[jj][1], acc[jj][2], kxx, kyy, kzz, kxy, -kxz, -kyz, mi[0], mi[1],
+                               mi[2]);
                 }
-                const T rr = rn;  // t_i / t_jj for this pair
-                if (P >= 1 && P - 1 + NS < NP && tid == 0) {
-                    // re-arm the stage of pair P - 1 with pair P - 1 + NS
-                    const int s1 = (P - 1) % NS;
-                    if (!s_abort && !mbar_wait(&empty[s1], ((P - 1) / NS) & 1, &g_wait_timeouts8))
-                        s_abort = 1;
-                    mbar_arrive_expect_tx(&full[s1], stage_bytes);
-                    bulk_copy_g2s(ring + s1 * stage_elems, tk + (size_t)(P - 1 + NS) * stage_elems, stage_bytes,
-                                  &full[s1]);
-                }
-                if (P + 1 < NP) {
-                    // the next pair is (i, jj + 1) or (i + 1, i + 1)
-                    const int s2 = (P + 1) % NS;
-                    const int jn = jj + 1 < L ? jj + 1 : i + 1;
-                    if (!*(volatile int *)&s_abort && !mbar_wait(&full[s2], ((P + 1) / NS) & 1, &g_wait_timeouts8))
-                        s_abort = 1;
-                    const T *kp = ring + s2 * stage_elems + q;
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) kn[c] = kp[c * QyS];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) mn[c] = mp[(3 * jn + c) * kCol8];
-                    rn = jj + 1 < L ? s_ratio[(jj + 1) * L + i] : (T)1;
-                }
-                block_fma8(acc[i][0], acc[i][1], acc[i][2], kc[0], kc[1], kc[2], kc[3], kc[4], kc[5], mc[0], mc[1],
-                           mc[2]);
-                if (jj != i)
-                    block_fma8(acc[jj][0], acc[jj][1], acc[jj][2], rr * kc[0], rr * kc[1], rr * kc[2],
-                               rr * kc[3], -rr * kc[4], -rr * kc[5], mi[0], mi[1], mi[2]);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[P % NS]);
             }
-        }
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            C *o = mp + 3 * l * kCol8;
-            o[0] = acc[l][0];
-            o[kCol8] = mir ? C{-acc[l][1].x, -acc[l][1].y} : acc[l][1];
-            o[2 * kCol8] = acc[l][2];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_row[i]);
+            // target i is complete (its reciprocal terms came from rows < i)
+            C *o = mp + 3 * i * kColR;
+            o[0] = acc[i][0];
+            o[kColR] = mir ? C{-acc[i][1].x, -acc[i][1].y} : acc[i][1];
+            o[2 * kColR] = acc[i][2];
         }
     }
+    if (!ok) s_abort = 1;
     __syncthreads();
-    if (s_abort && tid == 0) {
+    if (s_abort && tid == 512) {
         // a wait gave up: let the copies still in flight land (bounded) before exit
-#pragma unroll
-        for (int s = 0; s < NS; ++s) mbar_wait(&full[s], ((NP - 1 - s) / NS) & 1, &g_wait_timeouts8);
+        for (int r = 0; r < L; ++r) mbar_wait(&full_row[r], 0, &g_wait_timeouts8);
     }
+    if (producer) return;
 
     // inverse transforms: pass 1 in shared memory, pass 3 to global memory
     load_twiddles8<true>(w2, w3, tw, j);
@@ -624,9 +677,9 @@ __global__ void __launch_bounds__(512, 1) k_columns_ring8(float2 *__restrict__ s
     for (int u = 0; u < CPG; ++u) {
         const int c = group + 8 * u;
         if (c < NC) {
-            const C *col = cols + c * kCol8 + bj;
+            const C *col = cols + c * kColR + bs.bj;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
+            for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
         }
     }
     group_sync(group);
@@ -635,23 +688,18 @@ __global__ void __launch_bounds__(512, 1) k_columns_ring8(float2 *__restrict__ s
         const int c = group + 8 * u;
         if (c < NC) {
             dft8<true>(v[u]);
-            C *col = cols + c * kCol8 + b1;
+            C *col = cols + c * kColR + bs.b1;
 #pragma unroll
             for (int r = 0; r < 8; ++r) col[r] = v[u][r];
         }
     }
     group_sync(group);
-    ring8_pass2<true, CPG>(cols, group, NC, bj, b2, w2, v);
+    ring8_pass2<true, CPG>(cols, group, NC, bs, w2, v);
+    ring8_pass3<true, CPG>(cols, group, NC, bs, w3, v, false);
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
         const int c = group + 8 * u;
         if (c < NC) {
-            const C *col = cols + c * kCol8 + bj;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];
-#pragma unroll
-            for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w3[r - 1]);
-            dft8<true>(v[u]);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int y = j + 64 * r;
@@ -663,27 +711,23 @@ __global__ void __launch_bounds__(512, 1) k_columns_ring8(float2 *__restrict__ s
 
 template <int L>
 static cudaError_t launch_ring8(const ApplyArgs &a, cudaStream_t st) {
-    using R = Ring8<L>;
-    const size_t smem = (size_t)R::kCols * kCol8 * sizeof(float2) + (size_t)R::kStages * 6 * a.QyS * sizeof(float);
+    const size_t smem = Ring8<L>::kSmem;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_columns_ring8<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
     const int Kx = (1 << a.log2Px) / 2 + 1;
-    k_columns_ring8<L><<<dim3(Kx, a.B), 512, smem, st>>>((float2 *)a.spec, (const float *)a.tensor,
-                                                         (const float *)a.ratio, Kx, a.ny, a.QyS,
+    k_columns_ring8<L><<<dim3(Kx, a.B), 544, smem, st>>>((float2 *)a.spec, (const float *)a.tensor,
+                                                         (const float *)a.ratio, Kx, a.ny,
                                                          (const float2 *)a.twy);
     return cudaGetLastError();
 }
 
 // The streamed kernel takes float plans with L <= 8, the pair-symmetric
-// tensor, a 16-byte stage size and a 16-byte aligned tensor.
+// tensor with 260 stored frequencies per row and a 16-byte aligned tensor.
 static bool ring8_supported(const ApplyArgs &a, bool fp64) {
-    if (fp64 || a.full_pairs || a.L < 1 || a.L > 8 || a.QyS % 4 != 0) return false;
-    if ((reinterpret_cast<uintptr_t>(a.tensor) & 15) != 0) return false;
-    const size_t smem = (size_t)3 * a.L * kCol8 * sizeof(float2) +
-                        (size_t)std::min(a.L * (a.L + 1) / 2, 16) * 6 * a.QyS * sizeof(float);
-    return smem <= 227 * 1024;
+    if (fp64 || a.full_pairs || a.L < 1 || a.L > 8 || a.QyS != kQyS8 || a.log2Py != 9) return false;
+    return (reinterpret_cast<uintptr_t>(a.tensor) & 15) == 0;
 }
 
 static cudaError_t launch_ring8_any(const ApplyArgs &a, cudaStream_t st) {
