@@ -67,144 +67,6 @@ __device__ __forceinline__ void prefetch_l2_8(const void *p, size_t bytes) {
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
-                                                      typename cpx_of<T>::type *__restrict__ spec,
-                                                      int nx, int ny,
-                                                      const typename cpx_of<T>::type *__restrict__ tw,
-                                                      const T *__restrict__ layer_scale, int L) {
-    using C = typename cpx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);  // 8 row pairs x kCol8
-    const int Kx = kN8 / 2 + 1;
-    const int plane = blockIdx.y, y0 = blockIdx.x * 16;
-    const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
-    const T *mp = m + (size_t)plane * ny * nx;
-    const T sc = layer_scale ? layer_scale[(plane / 3) % L] : (T)1;
-    // pass 1 (Ns = 1) straight from global memory: pairs group and group + 4,
-    // z = row_a + i row_b, x = j + 64 r, zero for x >= nx (all r >= 4)
-    C v[2][8];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int q = group + 4 * h, ya = y0 + 2 * q, yb = ya + 1;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int x = j + 64 * r;
-            T a = 0, bv = 0;
-            if (x < nx) {
-                if (ya < ny) a = mp[(size_t)ya * nx + x];
-                if (yb < ny) bv = mp[(size_t)yb * nx + x];
-            }
-            v[h][r] = C{sc * a, sc * bv};
-        }
-#pragma unroll
-        for (int r = 4; r < 8; ++r) v[h][r] = C{0, 0};
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        dft8<false>(v[h]);
-        C *col = buf + (group + 4 * h) * kCol8;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) col[pad8i(8 * j + r)] = v[h][r];
-    }
-    group_sync(group);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) passes23<false>(buf + (group + 4 * h) * kCol8, j, tw, group, v[h], true);
-    __syncthreads();
-    // A[k] = (Z[k] + conj Z[-k]) / 2,  B[k] = (Z[k] - conj Z[-k]) / (2i)
-    C *sp = spec + (size_t)plane * Kx * ny;
-    for (int e = threadIdx.x; e < Kx * 16; e += 256) {
-        const int kx = e >> 4, r = e & 15;
-        const int y = y0 + r;
-        if (y >= ny) continue;
-        const C *zb = buf + (r >> 1) * kCol8;
-        const C z1 = zb[pad8i(kx)], z2 = zb[pad8i((kN8 - kx) & (kN8 - 1))];
-        C o;
-        if ((r & 1) == 0)
-            o = C{(T)0.5 * (z1.x + z2.x), (T)0.5 * (z1.y - z2.y)};
-        else
-            o = C{(T)0.5 * (z1.y + z2.y), (T)0.5 * (z2.x - z1.x)};
-        sp[(size_t)kx * ny + y] = o;
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>::type *__restrict__ spec,
-                                                      T *__restrict__ H, int nx, int ny,
-                                                      const typename cpx_of<T>::type *__restrict__ tw,
-                                                      T out_scale, const T *__restrict__ layer_scale,
-                                                      int L) {
-    using C = typename cpx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
-    const int half = kN8 / 2, Kx = half + 1;
-    const int plane = blockIdx.y, y0 = blockIdx.x * 16;
-    const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
-    const C *sp = spec + (size_t)plane * Kx * ny;
-    const T scale = out_scale * (layer_scale ? layer_scale[(plane / 3) % L] : (T)1);
-    // Z[kx] = A + iB, Z[512 - kx] = conj(A) + i conj(B); DC and Nyquist real
-    const int total = Kx * 8;
-    for (int base = threadIdx.x; base < total; base += 256 * 4) {
-        C A[4], Bv[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int e = base + k * 256;
-            const int kx = e >> 3, q = e & 7;
-            const int ya = y0 + 2 * q, yb = ya + 1;
-            A[k] = C{0, 0};
-            Bv[k] = C{0, 0};
-            if (e < total) {
-                if (ya < ny) A[k] = sp[(size_t)kx * ny + ya];
-                if (yb < ny) Bv[k] = sp[(size_t)kx * ny + yb];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int e = base + k * 256;
-            if (e >= total) continue;
-            const int kx = e >> 3, q = e & 7;
-            C a = A[k], bv = Bv[k];
-            if (kx == 0 || kx == half) {
-                a.y = 0;
-                bv.y = 0;
-            }
-            C *zb = buf + q * kCol8;
-            zb[pad8i(kx)] = C{a.x - bv.y, a.y + bv.x};
-            if (kx != 0 && kx != half) zb[pad8i(kN8 - kx)] = C{a.x + bv.y, bv.x - a.y};
-        }
-    }
-    __syncthreads();
-    C v[2][8];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const C *col = buf + (group + 4 * h) * kCol8;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[h][r] = col[pad8i(j + 64 * r)];
-    }
-    group_sync(group);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        dft8<true>(v[h]);
-        C *col = buf + (group + 4 * h) * kCol8;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) col[pad8i(8 * j + r)] = v[h][r];
-    }
-    group_sync(group);
-    T *hp = H + (size_t)plane * ny * nx;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        passes23<true>(buf + (group + 4 * h) * kCol8, j, tw, group, v[h], false);
-        const int q = group + 4 * h, ya = y0 + 2 * q, yb = ya + 1;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int x = j + 64 * r;
-            if (x >= nx) continue;
-            if (ya < ny) hp[(size_t)ya * nx + x] = scale * v[h][r].x;
-            if (yb < ny) hp[(size_t)yb * nx + x] = scale * v[h][r].y;
-        }
-    }
-}
-
 // Pair index of (a <= b) in the row-by-row numbering.
 __device__ __forceinline__ int pair_index8(int a, int b, int L) {
     return a * L - (a * (a - 1)) / 2 + (b - a);
@@ -442,15 +304,16 @@ struct Bases8 {
         : b1(8 * j + (j >> 1)), bj(j + (j >> 4)), b2(68 * (j >> 3) + (j & 7)) {}
 };
 
-// Pass 2 of the group's columns, shared memory to shared memory.
-template <bool INV, int CPG, typename C>
+// Pass 2 of the group's columns c = group + CSTEP u (column stride STRIDE),
+// shared memory to shared memory.
+template <bool INV, int CPG, int STRIDE, int CSTEP, typename C>
 __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const Bases8 &bs, const C (&w2)[7],
                                             C (&v)[CPG][8]) {
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
-        const int c = group + 8 * u;
+        const int c = group + CSTEP * u;
         if (c < ncol) {
-            const C *col = cols + c * kColR + bs.bj;
+            const C *col = cols + c * STRIDE + bs.bj;
 #pragma unroll
             for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
         }
@@ -458,12 +321,12 @@ __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const 
     group_sync(group);
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
-        const int c = group + 8 * u;
+        const int c = group + CSTEP * u;
         if (c < ncol) {
 #pragma unroll
             for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w2[r - 1]);
             dft8<INV>(v[u]);
-            C *col = cols + c * kColR + bs.b2;
+            C *col = cols + c * STRIDE + bs.b2;
 #pragma unroll
             for (int r = 0; r < 8; ++r) col[8 * r + (r >> 1)] = v[u][r];
         }
@@ -472,14 +335,14 @@ __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const 
 }
 
 // Pass 3 in place (positions j + 64 r), result left in v.
-template <bool INV, int CPG, typename C>
+template <bool INV, int CPG, int STRIDE, int CSTEP, typename C>
 __device__ __forceinline__ void ring8_pass3(C *cols, int group, int ncol, const Bases8 &bs, const C (&w3)[7],
                                             C (&v)[CPG][8], bool store) {
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
-        const int c = group + 8 * u;
+        const int c = group + CSTEP * u;
         if (c < ncol) {
-            C *col = cols + c * kColR + bs.bj;
+            C *col = cols + c * STRIDE + bs.bj;
 #pragma unroll
             for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
 #pragma unroll
@@ -581,8 +444,8 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
             }
         }
         group_sync(group);
-        ring8_pass2<false, CPG>(cols, group, NC, bs, w2, v);
-        ring8_pass3<false, CPG>(cols, group, NC, bs, w3, v, true);
+        ring8_pass2<false, CPG, kColR, 8>(cols, group, NC, bs, w2, v);
+        ring8_pass3<false, CPG, kColR, 8>(cols, group, NC, bs, w3, v, true);
     }
     __syncthreads();
 
@@ -694,8 +557,8 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
         }
     }
     group_sync(group);
-    ring8_pass2<true, CPG>(cols, group, NC, bs, w2, v);
-    ring8_pass3<true, CPG>(cols, group, NC, bs, w3, v, false);
+    ring8_pass2<true, CPG, kColR, 8>(cols, group, NC, bs, w2, v);
+    ring8_pass3<true, CPG, kColR, 8>(cols, group, NC, bs, w3, v, false);
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
         const int c = group + 8 * u;
@@ -705,6 +568,164 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
                 const int y = j + 64 * r;
                 if (y < ny) sp[(size_t)c * Kx * ny + y] = v[u][r];
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row transforms for Px = 512: 16 rows of one plane per 256-thread block, the
+// rows taken in pairs as one complex transform (z = row_a + i row_b), two
+// pairs per 64-thread group.  Same shared-memory layout as the column kernel
+// (one pad slot per 16) with an odd column stride, so the untangling step,
+// which reads eight columns at once, spreads over the banks as well.
+constexpr int kColRow = kN8 + kN8 / 16 + 1;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
+                                                      typename cpx_of<T>::type *__restrict__ spec,
+                                                      int nx, int ny,
+                                                      const typename cpx_of<T>::type *__restrict__ tw,
+                                                      const T *__restrict__ layer_scale, int L) {
+    using C = typename cpx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);  // 8 row pairs x kColRow
+    constexpr int Kx = kN8 / 2 + 1;
+    const int plane = blockIdx.y, y0 = blockIdx.x * 16;
+    const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
+    const T *mp = m + (size_t)plane * ny * nx;
+    const T sc = layer_scale ? layer_scale[(plane / 3) % L] : (T)1;
+    const Bases8 bs(j);
+    // pass 1 straight from global memory (x = j + 64 r; zero for x >= nx and r >= 4)
+    C v[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = group + 4 * h, ya = y0 + 2 * q, yb = ya + 1;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int x = j + 64 * r;
+            T a = 0, b = 0;
+            if (x < nx) {
+                if (ya < ny) a = mp[(size_t)ya * nx + x];
+                if (yb < ny) b = mp[(size_t)yb * nx + x];
+            }
+            v[h][r] = C{sc * a, sc * b};
+        }
+#pragma unroll
+        for (int r = 4; r < 8; ++r) v[h][r] = C{0, 0};
+    }
+    C w2[7], w3[7];
+    load_twiddles8<false>(w2, w3, tw, j);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        dft8<false>(v[h]);
+        C *col = buf + (group + 4 * h) * kColRow + bs.b1;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) col[r] = v[h][r];
+    }
+    group_sync(group);
+    ring8_pass2<false, 2, kColRow, 4>(buf, group, 8, bs, w2, v);
+    ring8_pass3<false, 2, kColRow, 4>(buf, group, 8, bs, w3, v, true);
+    __syncthreads();
+    // A[k] = (Z[k] + conj Z[-k]) / 2,  B[k] = (Z[k] - conj Z[-k]) / (2i)
+    C *sp = spec + (size_t)plane * Kx * ny;
+    for (int e = threadIdx.x; e < Kx * 16; e += 256) {
+        const int kx = e >> 4, r = e & 15;
+        const int y = y0 + r;
+        if (y >= ny) continue;
+        const C *zb = buf + (r >> 1) * kColRow;
+        const C z1 = zb[pad16(kx)], z2 = zb[pad16((kN8 - kx) & (kN8 - 1))];
+        C o;
+        if ((r & 1) == 0)
+            o = C{(T)0.5 * (z1.x + z2.x), (T)0.5 * (z1.y - z2.y)};
+        else
+            o = C{(T)0.5 * (z1.y + z2.y), (T)0.5 * (z2.x - z1.x)};
+        sp[(size_t)kx * ny + y] = o;
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ C shfl_xor_c(C v, int mask) {
+    return C{__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask)};
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>::type *__restrict__ spec,
+                                                      T *__restrict__ H, int nx, int ny,
+                                                      const typename cpx_of<T>::type *__restrict__ tw,
+                                                      T out_scale, const T *__restrict__ layer_scale,
+                                                      int L) {
+    using C = typename cpx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);  // 8 row pairs x kColRow
+    constexpr int half = kN8 / 2, Kx = half + 1;
+    constexpr int NIT = half * 16 / 256;  // spectrum entries per thread for kx < 256
+    const int plane = blockIdx.y, y0 = blockIdx.x * 16;
+    const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
+    const C *sp = spec + (size_t)plane * Kx * ny;
+    const T scale = out_scale * (layer_scale ? layer_scale[(plane / 3) % L] : (T)1);
+    // thread (kx, r) reads row y0 + r at kx, coalesced (16 rows of one kx are
+    // contiguous); lanes r and r ^ 1 trade A (row a) and B (row b) of pair r / 2
+    const int r = threadIdx.x & 15, y = y0 + r;
+    C in[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int kx = (threadIdx.x >> 4) + 16 * it;
+        in[it] = y < ny ? sp[(size_t)kx * ny + y] : C{0, 0};
+    }
+    const C nyq = (threadIdx.x < 16 && y < ny) ? sp[(size_t)half * ny + y] : C{0, 0};
+    C *zb = buf + (r >> 1) * kColRow;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int kx = (threadIdx.x >> 4) + 16 * it;
+        const C other = shfl_xor_c(in[it], 1);
+        C A = (r & 1) ? other : in[it], B = (r & 1) ? in[it] : other;
+        if (kx == 0) {
+            A.y = 0;
+            B.y = 0;
+        }
+        // Z[kx] = A + i B, Z[512 - kx] = conj(A) + i conj(B)
+        if ((r & 1) == 0)
+            zb[pad16(kx)] = C{A.x - B.y, A.y + B.x};
+        else if (kx != 0)
+            zb[pad16(kN8 - kx)] = C{A.x + B.y, B.x - A.y};
+    }
+    if (threadIdx.x < 32) {
+        const C other = shfl_xor_c(nyq, 1);
+        if (threadIdx.x < 16 && (r & 1) == 0) zb[pad16(half)] = C{nyq.x, other.x};  // A, B real at Nyquist
+    }
+    __syncthreads();
+    // inverse transforms: pass 1 in shared memory, pass 3 straight to global
+    const Bases8 bs(j);
+    C w2[7], w3[7];
+    load_twiddles8<true>(w2, w3, tw, j);
+    C v[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const C *col = buf + (group + 4 * h) * kColRow + bs.bj;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[h][q] = col[68 * q];
+    }
+    group_sync(group);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        dft8<true>(v[h]);
+        C *col = buf + (group + 4 * h) * kColRow + bs.b1;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) col[q] = v[h][q];
+    }
+    group_sync(group);
+    ring8_pass2<true, 2, kColRow, 4>(buf, group, 8, bs, w2, v);
+    ring8_pass3<true, 2, kColRow, 4>(buf, group, 8, bs, w3, v, false);
+    T *hp = H + (size_t)plane * ny * nx;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = group + 4 * h, ya = y0 + 2 * q, yb = ya + 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = j + 64 * k;
+            if (x >= nx) continue;
+            if (ya < ny) hp[(size_t)ya * nx + x] = scale * v[h][k].x;
+            if (yb < ny) hp[(size_t)yb * nx + x] = scale * v[h][k].y;
         }
     }
 }
@@ -758,7 +779,7 @@ bool cols512_supported(int log2Py, int L, bool fp64) {
 template <typename T>
 cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forward, cudaStream_t st) {
     using C = typename cpx_of<T>::type;
-    const size_t smem = (size_t)8 * kCol8 * sizeof(C);
+    const size_t smem = (size_t)8 * kColRow * sizeof(C);
     const dim3 grid((a.ny + 15) / 16, a.B * a.L * 3);
     cudaError_t e;
     if (forward) {
