@@ -85,6 +85,30 @@ const char *demag_last_error(void);
 demag_status demag_wait_timeouts(unsigned long long *count);
 
 /*
+ * demag_selftest_bounded_wait - exercise the bounded-wait path on the GPU.
+ *
+ * Not a step of the paper's method: a test of the mechanism above.  Launches
+ * one thread that waits on a shared-memory barrier which nothing can
+ * complete; the wait gives up after limit_cycles SM clock cycles (1 to 2^31)
+ * and counts one timeout, which the next demag_wait_timeouts() reports.  The
+ * kernel then returns normally: nothing hangs or faults.  Synchronises
+ * `stream`.  DEMAG_EINVAL for a limit out of range, DEMAG_ECUDA on a CUDA
+ * error.
+ */
+demag_status demag_selftest_bounded_wait(long long limit_cycles, void *stream);
+
+/*
+ * demag_debug_fail_alloc - host-side fault injection for tests.
+ *
+ * Not a step of the paper's method.  After `after` further device allocations
+ * by the library, the next one is refused as if cudaMalloc had run out of
+ * memory (the call that needed it returns DEMAG_ENOMEM and frees what it had
+ * allocated); the injection then switches itself off.  after < 0 switches it
+ * off at once.  Process-wide, not thread-safe; always returns DEMAG_OK.
+ */
+demag_status demag_debug_fail_alloc(int after);
+
+/*
  * demag_plan_create - build the Fourier-space layer tensor of a layer stack.
  *
  * Sec. 2 (generalized Newell tensor) and Sec. 3 (Eq. FFT_v2).  For every pair

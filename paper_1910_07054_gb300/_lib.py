@@ -89,6 +89,10 @@ def lib():
     L.demag_destroy.restype = i
     L.demag_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
     L.demag_wait_timeouts.restype = i
+    L.demag_selftest_bounded_wait.argtypes = [ctypes.c_longlong, vp]
+    L.demag_selftest_bounded_wait.restype = i
+    L.demag_debug_fail_alloc.argtypes = [i]
+    L.demag_debug_fail_alloc.restype = i
     _lib = L
     return L
 
@@ -325,6 +329,16 @@ def demag_wait_timeouts():
     n = ctypes.c_ulonglong(0)
     _check(lib().demag_wait_timeouts(ctypes.byref(n)), "demag_wait_timeouts")
     return int(n.value)
+
+
+def demag_selftest_bounded_wait(limit_cycles, stream=None):
+    """Run one bounded wait that cannot complete (it gives up after limit_cycles)."""
+    _check(lib().demag_selftest_bounded_wait(int(limit_cycles), _stream(stream)), "demag_selftest_bounded_wait")
+
+
+def demag_debug_fail_alloc(after):
+    """Refuse the library's device allocation after the next `after` ones (host-side injection)."""
+    _check(lib().demag_debug_fail_alloc(int(after)), "demag_debug_fail_alloc")
 
 
 def demag_destroy(plan):

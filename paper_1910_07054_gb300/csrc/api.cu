@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "mbar.cuh"
 #include "layout.cuh"
 
 namespace demag {
@@ -64,7 +65,15 @@ static void free_plan(demag_plan *p) {
 }
 
 // Device allocation that records the failure.
+// Host-side fault injection (demag_debug_fail_alloc): allocations left before
+// one is refused; negative = off.
+static int g_alloc_fail_after = -1;
+
 static demag_status dalloc(void **ptr, size_t bytes, const char *what) {
+    if (g_alloc_fail_after >= 0 && g_alloc_fail_after-- == 0) {
+        *ptr = nullptr;
+        return fail(DEMAG_ENOMEM, std::string("cudaMalloc(") + what + "): refused by demag_debug_fail_alloc");
+    }
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -223,6 +232,21 @@ const char *demag_status_string(demag_status s) {
 }
 
 const char *demag_last_error(void) { return g_last_error.c_str(); }
+
+demag_status demag_debug_fail_alloc(int after) {
+    g_alloc_fail_after = after < 0 ? -1 : after;
+    return DEMAG_OK;
+}
+
+demag_status demag_selftest_bounded_wait(long long limit_cycles, void *stream) {
+    if (limit_cycles < 1 || limit_cycles > kWaitLimitCycles)
+        return fail(DEMAG_EINVAL, "limit_cycles must be in [1, 2^31]");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_selftest_wait(limit_cycles, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self test");
+    return DEMAG_OK;
+}
 
 demag_status demag_wait_timeouts(unsigned long long *count) {
     if (!count) return fail(DEMAG_EINVAL, "count is NULL");

@@ -764,6 +764,20 @@ static cudaError_t launch_ring8_any(const ApplyArgs &a, cudaStream_t st) {
     }
 }
 
+// One thread waits on a barrier that no arrival or copy can complete, so the
+// bounded wait must give up after `limit` cycles and count one timeout.
+__global__ void k_selftest_wait(long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    mbar_wait(&bar, 0, &g_wait_timeouts8, limit);
+}
+
+cudaError_t launch_selftest_wait(long long limit, cudaStream_t st) {
+    k_selftest_wait<<<1, 1, 0, st>>>(limit);
+    return cudaGetLastError();
+}
+
 unsigned take_wait_timeouts() {
     unsigned n = 0, zero = 0;
     if (cudaMemcpyFromSymbol(&n, g_wait_timeouts8, sizeof(n)) != cudaSuccess) return ~0u;

@@ -102,6 +102,8 @@ cudaError_t launch_cols512(const ApplyArgs &a, cudaStream_t st);
 // Bounded waits of the streamed column kernel that gave up since the last
 // call (the count is cleared); ~0u if the counter could not be read.
 unsigned take_wait_timeouts();
+// One block whose single bounded wait cannot complete (gives up after `limit` cycles).
+cudaError_t launch_selftest_wait(long long limit, cudaStream_t st);
 
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);

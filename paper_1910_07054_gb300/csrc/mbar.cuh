@@ -49,12 +49,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 }
 
 // Waits for the phase of the given parity to complete; false (and one count
-// in *timeouts) if it has not after kWaitLimitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned *timeouts) {
+// in *timeouts) if it has not after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned *timeouts,
+                                          long long limit = kWaitLimitCycles) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitLimitCycles) {
+        if (clock64() - t0 > limit) {
             atomicAdd(timeouts, 1u);
             return false;
         }
