@@ -41,6 +41,10 @@ def parse_args():
                    help="seconds of oracle evaluation for the CPU baseline sample")
     p.add_argument("--no-parity", action="store_true", help="skip the oracle field comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--batched-only", action="store_true",
+                   help="run only the batched split-precision measurement and print its JSON")
+    p.add_argument("--batched-n", type=int, default=512,
+                   help="in-plane cells per side of the batched measurement (smaller for profiling)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched (512x512x64, 16 states) and surrogate measurements")
     return p.parse_args()
@@ -210,10 +214,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_measurement(steps, peaks):
-    """512 x 512 cells, 64 layers, 16 states per apply: the split-precision
-    tensor-core contraction (path 4) against the same products on the FP32
-    cores (path 3), same plan, same data movement."""
+def batched_measurement(steps, peaks, n=512):
+    """512 x 512 cells (n x n if given), 64 layers, 16 states per apply: the
+    split-precision tensor-core contraction (path 4) against the same products
+    on the FP32 cores (path 3), same plan, same data movement."""
     import numpy as np
     import torch
 
@@ -221,17 +225,18 @@ def batched_measurement(steps, peaks):
     from paper_1910_07054_gb300 import inputs
     c = inputs.CONFIGS["scale512"]
     th = [float(t) for t in inputs.thicknesses("scale512")]
-    nx, ny, B, L = c["nx"], c["ny"], c["batch"], len(th)
+    nx, ny, B, L = n, n, c["batch"], len(th)
     t0 = time.perf_counter()
     plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     m = torch.tensor(inputs.random_unit_vectors((B, L, ny, nx), seed=0), dtype=torch.float32, device="cuda")
     H = torch.empty_like(m)
-    out = {"workload": "512x512 cells of 2x2 nm, 64 layers (t ~ U[0.5, 3] nm, seed 0), 16 random "
-                       "states per apply; inputs (3.2 GB) exceed L2", "plan_create_s": build_s}
+    out = {"workload": "%dx%d cells of 2x2 nm, 64 layers (t ~ U[0.5, 3] nm, seed 0), 16 random "
+                       "states per apply; inputs (%.2f GB)" % (nx, ny, B * L * 3 * nx * ny * 4 / 1e9),
+           "plan_create_s": build_s}
     fields = {}
-    for path, name in ((4, "tensor_cores_3xtf32"), (3, "fp32_cores")):
+    for path, name in ((4, "tensor_cores_3xtf32"), (6, "tcgen05_3xtf32"), (3, "fp32_cores")):
         dm.demag_plan_set_path(plan.handle, path)
         info = dm.demag_plan_info(plan.handle)
         dm.demag_apply(plan.handle, m, inputs.MS_DEFAULT, H, info=info)
@@ -246,15 +251,19 @@ def batched_measurement(steps, peaks):
                                     "rows_inverse": float(st[2])},
                      "contraction_tflops_useful": flops / (st[4] * 1e-3) / 1e12}
     tf32_peak = peaks.get("bf16_tflops", 1894.6) * (1.1 / 2.25)
+    for name in ("tensor_cores_3xtf32", "tcgen05_3xtf32"):
+        tc = out[name]
+        tc["roofline"] = {"bound": "tensor", "achieved": 3 * tc["contraction_tflops_useful"],
+                          "peak": tf32_peak, "unit": "TFLOP/s",
+                          "frac": 3 * tc["contraction_tflops_useful"] / tf32_peak,
+                          "note": "TF32 issue rate (3 passes per useful flop) against the measured bf16 "
+                                  "burst peak x nominal tf32/bf16 ratio (1.1/2.25)"}
     tc = out["tensor_cores_3xtf32"]
-    tc["roofline"] = {"bound": "tensor", "achieved": 3 * tc["contraction_tflops_useful"],
-                      "peak": tf32_peak, "unit": "TFLOP/s",
-                      "frac": 3 * tc["contraction_tflops_useful"] / tf32_peak,
-                      "note": "TF32 issue rate (3 passes per useful flop) against the measured bf16 "
-                              "burst peak x nominal tf32/bf16 ratio (1.1/2.25)"}
     d = fields[4] - fields[3]
     out["rel_l2_between_variants"] = float(torch.linalg.vector_norm(d.double()) /
                                            torch.linalg.vector_norm(fields[3].double()))
+    out["rel_l2_tcgen05_vs_fp32_cores"] = float(torch.linalg.vector_norm((fields[6] - fields[3]).double()) /
+                                                torch.linalg.vector_norm(fields[3].double()))
     out["speedup_tensor_vs_fp32_cores"] = out["fp32_cores"]["ms_per_apply"] / tc["ms_per_apply"]
     plan.close()
     return out
@@ -452,6 +461,13 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    if args.batched_only:
+        peaks = {}
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                peaks = json.load(fh)
+        print(json.dumps(batched_measurement(max(args.steps, 1), peaks, args.batched_n)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -127,7 +127,7 @@ demag_status demag_debug_fail_alloc(int after);
  *   precision  a demag_precision value; DEMAG_PREC_SPLIT_TF32 needs
  *              (6 L^2 + 12 L B + 12 L B) floats (L padded to 16, B to 8)
  *              within 220 KB of shared memory, and its tensor is stored in
- *              the layout [kx][u][pair][component] (see demag_plan_tensor)
+ *              the layout [kx][u][component][pair] (see demag_plan_tensor)
  *   max_batch  largest batch B later passed to demag_apply, >= 1
  *   stream     stream for the set-up work; the call synchronises this stream
  *              before it returns
@@ -170,14 +170,18 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
  *   path 3: (DEMAG_PREC_SPLIT_TF32 plans) column kernels of path 2 with the
  *           contraction as dense L x L by L x B products on the FP32 cores.
  *   path 4: (DEMAG_PREC_SPLIT_TF32 plans, their default) the same products
- *           on the tensor cores in three TF32 passes.
+ *           on the tensor cores in three TF32 passes (warp-level m16n8k8
+ *           TF32 MMAs, two blocks per SM).
  *   path 5: (reported, not selectable otherwise) the fused column kernel with
  *           the radix-8 512-point transforms, chosen by demag_plan_create
  *           when Py = 512 and the columns fit; its tensor is stored in
  *           natural folded-ky order, so such a plan runs path 5 only.
+ *   path 6: (DEMAG_PREC_SPLIT_TF32 plans, even L <= 64, max_batch <= 16) the
+ *           same products on the tcgen05 tensor cores: 3xTF32, accumulators
+ *           in tensor memory, one persistent block per SM.
  *   path 0: the default choice of demag_plan_create (5 or 1 when it fits,
  *           else 2; 4 for DEMAG_PREC_SPLIT_TF32).
- * Both paths compute the same field (Eq. FFT_v2); this entry point exists to
+ * All paths compute the same field (Eq. FFT_v2); this entry point exists to
  * test and time them against each other.  Errors: DEMAG_EINVAL, DEMAG_ENOMEM,
  * DEMAG_EUNSUPPORTED (the path cannot hold this plan).
  */
@@ -279,8 +283,9 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
  *
  * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,
  * layout [kx][pair][component][u] (DEMAG_PREC_SPLIT_TF32 plans:
- * (Px/2+1) * (Py/2+1) * NB floats, layout [kx][u][pair][component] with
- * NB = npairs * 6 rounded up to a multiple of 4, the padding zero)
+ * (Px/2+1) * (Py/2+1) * NB floats, layout [kx][u][component][pair] with
+ * each component row npairs rounded up to a multiple of 4 (NB = 6 times
+ * that), the padding zero)
  * with pair (i <= j) numbered row by row
  * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components
  * {Re N_xx, Re N_yy, Re N_zz, Re N_xy, Im N_xz, Im N_yz} of the 2D DFT of

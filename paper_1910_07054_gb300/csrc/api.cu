@@ -252,9 +252,9 @@ demag_status demag_wait_timeouts(unsigned long long *count) {
     if (!count) return fail(DEMAG_EINVAL, "count is NULL");
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    const unsigned n = take_wait_timeouts();
-    if (n == ~0u) return fail(DEMAG_ECUDA, "cannot read the wait-timeout counter");
-    *count = n;
+    const unsigned n = take_wait_timeouts(), n5 = take_tc_timeouts();
+    if (n == ~0u || n5 == ~0u) return fail(DEMAG_ECUDA, "cannot read the wait-timeout counters");
+    *count = (unsigned long long)n + n5;
     return DEMAG_OK;
 }
 
@@ -475,9 +475,11 @@ demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     const bool fp64 = plan->precision == DEMAG_PREC_FP64;
     if (plan->umajor) {
         if (path == 0) path = 4;
-        if (path != 3 && path != 4)
-            return fail(DEMAG_EUNSUPPORTED, "split-TF32 plans run path 3 or 4");
-        plan->contract_mode = path == 4 ? 2 : 1;
+        if (path != 3 && path != 4 && path != 6)
+            return fail(DEMAG_EUNSUPPORTED, "split-TF32 plans run path 3, 4 or 6");
+        if (path == 6 && !tc5_supported(plan->L, plan->max_batch, plan->npairs))
+            return fail(DEMAG_EUNSUPPORTED, "path 6 needs an even L <= 64 and max_batch <= 16");
+        plan->contract_mode = path == 4 ? 2 : (path == 6 ? 3 : 1);
         return DEMAG_OK;
     }
     if (path == 3 || path == 4)
@@ -579,7 +581,7 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     out[6] = plan->max_batch;
     out[7] = plan->npairs;
     out[8] = plan->QyS;
-    out[9] = plan->umajor ? (plan->contract_mode == 2 ? 4 : 3)
+    out[9] = plan->umajor ? (plan->contract_mode == 2 ? 4 : (plan->contract_mode == 3 ? 6 : 3))
                           : (plan->split ? 2 : (plan->natural ? 5 : 1));
     return DEMAG_OK;
 }

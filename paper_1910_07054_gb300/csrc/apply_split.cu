@@ -276,7 +276,8 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (iev && (e = cudaEventRecord(iev[1], st)) != cudaSuccess) return e;
     if (a.contract_mode != 0) {
-        if ((e = launch_contract_gemm(a, a.contract_mode == 2, st)) != cudaSuccess) return e;
+        e = a.contract_mode == 3 ? launch_contract_tc5(a, st) : launch_contract_gemm(a, a.contract_mode == 2, st);
+        if (e != cudaSuccess) return e;
         if (iev && (e = cudaEventRecord(iev[2], st)) != cudaSuccess) return e;
         k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec,
                                                                     a.ny, Kx, planes, G, a.log2Py,

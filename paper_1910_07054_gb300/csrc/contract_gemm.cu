@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
     __syncthreads();
     // compact tensor of the entry: npairs * 6 floats, contiguous and 16-byte
     // aligned; all loads of a thread are issued before any is used
-    const int NB = umajor_block(npairs);
+    const int NB = umajor_block(npairs), NR = umajor_row(npairs);
     const float4 *tu4 = reinterpret_cast<const float4 *>(tensor_um + ((size_t)kx * Qy + u) * NB);
     const int n4 = NB / 4;
     constexpr int kBatch = 8;
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int e = 4 * e4 + w;
-                if (e >= npairs * 6) break;  // block padding
-                const int P = e / 6, c = e - P * 6;
+                const int c = e / NR, P = e - c * NR;  // [component][pair] rows of NR
+                if (P >= npairs) continue;             // row padding
                 // pair P = (a, b), a <= b, numbered row by row: invert the
                 // triangular count from the end, r = T - 1 - P
                 const int T = L * (L + 1) / 2, r = T - 1 - P;
@@ -278,6 +278,203 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core contraction for B <= 16 (NT = Bp / 8 n-tiles), two blocks per SM.
+//
+// The compact tensor of the entry stays compact in shared memory: each
+// m16n8k8 A fragment element (target i, source j) is read from the stored
+// pair (min, max) and, for i > j, scaled by t_j / t_i = tau_j / tau_i
+// (tau_l = t_l / t_0) with xz and yz negated (reciprocity), so the six dense
+// L x L matrices are never formed.  Warp unit = (m-tile of 16 targets,
+// position); it keeps the six outputs of its unit in registers and, per
+// k-step, splits the 6 x NT state fragments once and each component's A
+// fragment once, then issues the 18 products (3 TF32 passes each).
+template <int NT>
+__global__ void __launch_bounds__(kGemmThreads, 2) k_contract_tc(float2 *__restrict__ spec2,
+                                                               const float *__restrict__ tensor_um,
+                                                               const float *__restrict__ ratio, int L, int B,
+                                                               int log2Py, int npairs) {
+    extern __shared__ __align__(16) float smem_f[];
+    const int Lp = pad16(L), Bp = 8 * NT, S = gemm_stride(Lp);
+    const int NB = umajor_block(npairs), NR = umajor_row(npairs);
+    float *raw = smem_f;                     // [6][NR]: the entry's component rows
+    float *Ms = smem_f + NB;                 // [2][6][Bp][S]: M_s[b][j]; later the output rows
+    float *s_tau = Ms + 2 * 6 * Bp * S;      // [Lp]: t_l / t_0
+    float *s_itau = s_tau + Lp;              // [Lp]: t_0 / t_l
+    const int Py = 1 << log2Py, Qy = Py / 2 + 1;
+    const int planes = B * 3 * L;
+    const int kx = blockIdx.x, u = blockIdx.y;
+    int p1, p2;
+    u_positions(u, log2Py, p1, p2);
+    const int ky1 = bit_reverse(p1, log2Py);
+    const int npos = p2 != p1 ? 2 : 1;
+    const int tid = threadIdx.x;
+
+    // compact tensor (contiguous, 16-byte aligned)
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(tensor_um + ((size_t)kx * Qy + u) * NB);
+        float4 *dst = reinterpret_cast<float4 *>(raw);
+        const int n4 = NB / 4;
+        constexpr int kBatch = 13;
+        for (int base = tid; base < n4; base += kGemmThreads * kBatch) {
+            float4 v[kBatch];
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k) {
+                const int e = base + k * kGemmThreads;
+                if (e < n4) v[k] = src[e];
+            }
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k) {
+                const int e = base + k * kGemmThreads;
+                if (e < n4) dst[e] = v[k];
+            }
+        }
+    }
+    if (tid < Lp) {
+        s_tau[tid] = tid < L ? ratio[tid] : 0.f;           // t_l / t_0
+        s_itau[tid] = tid < L ? ratio[tid * L] : 0.f;      // t_0 / t_l
+    }
+    if (Bp != B || Lp != L)
+        for (int e = tid; e < 2 * 6 * Bp * S; e += kGemmThreads) Ms[e] = 0.f;
+    __syncthreads();
+    // states at the entry's positions: element (b, j, c) of a position row is
+    // plane b * 3L + 3 j + c; thread r < 3L takes j = r / 3, c = r % 3 for every b
+    float2 *sk = spec2 + (size_t)kx * Py * planes;
+    if (tid < 3 * L) {
+        const int j = tid / 3, c = tid - 3 * (tid / 3);
+        for (int pos = 0; pos < npos; ++pos) {
+            const float2 *row = sk + (size_t)(pos ? p2 : p1) * planes + tid;
+            float *m = Ms + (size_t)pos * 6 * Bp * S;
+            for (int b0 = 0; b0 < B; b0 += 16) {
+                float2 v[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (b0 + k < B) v[k] = row[(size_t)(b0 + k) * 3 * L];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if (b0 + k >= B) break;
+                    m[(c * Bp + b0 + k) * S + j] = v[k].x;        // Mr_c
+                    m[((3 + c) * Bp + b0 + k) * S + j] = v[k].y;  // Mi_c
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int gr = lane >> 2, gc = lane & 3;
+    const int mtiles = Lp / 16;
+    // a warp holds at most one unit's accumulators across the final barrier
+    float acc[6][NT][4];
+    int my_mt = -1, my_q = 0;
+    for (int unit = warp; unit < mtiles * npos; unit += kGemmThreads / 32) {
+        const int mt = unit % mtiles, q = unit / mtiles;
+        // s = -1 at the mirrored frequency: xy and yz change sign
+        const bool neg_mirror = ((q == 0) == (ky1 > Py / 2));
+        const uint32_t smask = neg_mirror ? 0x80000000u : 0u;
+#pragma unroll
+        for (int o = 0; o < 6; ++o)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) acc[o][n][f] = 0.f;
+        const float *Mq = Ms + (size_t)q * 6 * Bp * S;
+        for (int k0 = 0; k0 < Lp; k0 += 8) {
+            uint32_t bh[6][NT][2], bl[6][NT][2];
+#pragma unroll
+            for (int st = 0; st < 6; ++st)
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    const float *bp = Mq + ((size_t)st * Bp + n * 8 + gr) * S + k0 + gc;
+                    const float b0 = bp[0], b1 = bp[4];
+                    bh[st][n][0] = to_tf32(b0);
+                    bh[st][n][1] = to_tf32(b1);
+                    bl[st][n][0] = to_tf32(b0 - __uint_as_float(bh[st][n][0]));
+                    bl[st][n][1] = to_tf32(b1 - __uint_as_float(bh[st][n][1]));
+                }
+            // fragment elements f: (row gr | gr + 8, column gc | gc + 4)
+            int base[4];
+            float scl[4];
+            bool rev[4];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const int i = mt * 16 + gr + ((f & 1) ? 8 : 0), jj = k0 + gc + ((f & 2) ? 4 : 0);
+                const int lo = i < jj ? i : jj, hi = i < jj ? jj : i;
+                base[f] = (i < L && jj < L) ? (lo * L - (lo * (lo - 1)) / 2 + (hi - lo)) : -1;
+                rev[f] = i > jj;
+                scl[f] = rev[f] ? s_tau[jj] * s_itau[i] : 1.f;
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                uint32_t ah[4], al[4];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    float v = base[f] >= 0 ? raw[c * NR + base[f]] * scl[f] : 0.f;
+                    if (c >= 4 && rev[f]) v = -v;
+                    ah[f] = to_tf32(v);
+                    al[f] = to_tf32(v - __uint_as_float(ah[f]));
+                }
+                // the component's terms: (output, state, sign mask)
+                auto term = [&](int o, int st, uint32_t mask) {
+                    uint32_t ahs[4], als[4];
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        ahs[f] = ah[f] ^ mask;
+                        als[f] = al[f] ^ mask;
+                    }
+#pragma unroll
+                    for (int n = 0; n < NT; ++n) {
+                        mma_tf32(acc[o][n], als, bh[st][n]);
+                        mma_tf32(acc[o][n], ahs, bl[st][n]);
+                        mma_tf32(acc[o][n], ahs, bh[st][n]);
+                    }
+                };
+                constexpr uint32_t NEG = 0x80000000u;
+                // states 0..5 = Mr_x, Mr_y, Mr_z, Mi_x, Mi_y, Mi_z; outputs 0..5 =
+                // Hr_x, Hi_x, Hr_y, Hi_y, Hr_z, Hi_z
+                if (c == 0) { term(0, 0, 0); term(1, 3, 0); }
+                if (c == 1) { term(2, 1, 0); term(3, 4, 0); }
+                if (c == 2) { term(4, 2, 0); term(5, 5, 0); }
+                if (c == 3) { term(0, 1, smask); term(1, 4, smask); term(2, 0, smask); term(3, 3, smask); }
+                if (c == 4) { term(0, 5, NEG); term(1, 2, 0); term(4, 3, NEG); term(5, 0, 0); }
+                if (c == 5) { term(2, 5, NEG ^ smask); term(3, 2, smask); term(4, 4, NEG ^ smask); term(5, 1, smask); }
+            }
+        }
+        my_mt = mt;
+        my_q = q;
+    }
+    __syncthreads();  // every warp is done with Ms: it now takes the output rows
+    if (my_mt >= 0) {
+        float *out = Ms + (size_t)my_q * 2 * planes;  // [b][i][c] complex
+#pragma unroll
+        for (int o = 0; o < 6; ++o)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const int i = my_mt * 16 + gr + (f >= 2 ? 8 : 0);
+                    const int b = n * 8 + 2 * gc + (f & 1);
+                    if (i < L && b < B) out[((b * L + i) * 3 + (o >> 1)) * 2 + (o & 1)] = acc[o][n][f];
+                }
+    }
+    __syncthreads();
+    for (int pos = 0; pos < npos; ++pos) {
+        float2 *dst = sk + (size_t)(pos ? p2 : p1) * planes;
+        if (planes % 2 == 0) {  // both ends 16-byte aligned
+            const float4 *src = reinterpret_cast<const float4 *>(Ms + (size_t)pos * 2 * planes);
+            for (int e = tid; e < planes / 2; e += kGemmThreads) reinterpret_cast<float4 *>(dst)[e] = src[e];
+        } else {
+            const float2 *src = reinterpret_cast<const float2 *>(Ms + (size_t)pos * 2 * planes);
+            for (int e = tid; e < planes; e += kGemmThreads) dst[e] = src[e];
+        }
+    }
+}
+
+size_t tc_smem_bytes(int L, int npairs) {
+    const int Lp = pad16(L), S = gemm_stride(Lp);
+    return (size_t)(umajor_block(npairs) + 2 * 6 * 16 * S + 2 * Lp) * sizeof(float);
+}
+
 }  // namespace demag
 
 namespace demag {
@@ -287,7 +484,24 @@ cudaError_t launch_contract_gemm(const ApplyArgs &a, bool tensor_cores, cudaStre
     const size_t smem = gemm_smem_bytes(a.L, a.B);
     cudaError_t e;
     dim3 grid(Kx, Qy);
-    if (tensor_cores) {
+    if (tensor_cores && a.B <= 16) {
+        const size_t sm = tc_smem_bytes(a.L, a.npairs);
+        if (a.B <= 8) {
+            if ((e = cudaFuncSetAttribute(k_contract_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+                cudaSuccess)
+                return e;
+            k_contract_tc<1><<<grid, kGemmThreads, sm, st>>>((float2 *)a.spec2, (const float *)a.tensor,
+                                                             (const float *)a.ratio, a.L, a.B, a.log2Py,
+                                                             a.npairs);
+        } else {
+            if ((e = cudaFuncSetAttribute(k_contract_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+                cudaSuccess)
+                return e;
+            k_contract_tc<2><<<grid, kGemmThreads, sm, st>>>((float2 *)a.spec2, (const float *)a.tensor,
+                                                             (const float *)a.ratio, a.L, a.B, a.log2Py,
+                                                             a.npairs);
+        }
+    } else if (tensor_cores) {
         if ((e = cudaFuncSetAttribute(k_contract_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem)) != cudaSuccess)
             return e;

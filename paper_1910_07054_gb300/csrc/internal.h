@@ -79,7 +79,8 @@ struct ApplyArgs {
     void *spec2 = nullptr;  // split path: [Kx][Py][B][L][3] complex workspace
     int split = 0;        // 1: column transforms and contraction in separate kernels
     int full_pairs = 0;   // 1: tensor holds all L*L pairs (no reciprocity)
-    int contract_mode = 0;  // split path: 0 per-item kernel, 1 dense products on
+    int contract_mode = 0;  // split path: 0 per-item kernel, 3 dense products on the
+                            // tcgen05 tensor cores (3xTF32, TMEM accumulators), 1 dense products on
                             // FP32 cores, 2 dense products on tensor cores (3xTF32)
     int natural = 0;      // 512-point column kernel, tensor in natural folded-ky order
     cudaEvent_t *inner_ev = nullptr;  // split path, optional [4]: before and after its 3 kernels
@@ -104,6 +105,11 @@ cudaError_t launch_cols512(const ApplyArgs &a, cudaStream_t st);
 unsigned take_wait_timeouts();
 // One block whose single bounded wait cannot complete (gives up after `limit` cycles).
 cudaError_t launch_selftest_wait(long long limit, cudaStream_t st);
+
+// Dense-product contraction on the tcgen05 tensor cores (contract_tc5.cu).
+bool tc5_supported(int L, int B, int npairs);
+cudaError_t launch_contract_tc5(const ApplyArgs &a, cudaStream_t st);
+unsigned take_tc_timeouts();
 
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);
@@ -131,7 +137,7 @@ struct demag_plan {
     void *d_spec2 = nullptr;      // split path workspace
     int split = 0;                // 1: split path
     int contract_mode = 0;        // split path contraction (see ApplyArgs)
-    int umajor = 0;               // tensor layout [Kx][Qy][npairs][6] (split-TF32 plans)
+    int umajor = 0;               // tensor layout [Kx][Qy][6][npairs padded] (split-TF32 plans)
     int natural = 0;              // fused 512-point column kernel, natural folded-ky tensor
     void *d_tscale = nullptr;     // [2L]: t_l, then 1 / t_l (plan real type)
     void *d_dtensor = nullptr;    // d N / d t_dlayer, all L*L pairs, [Kx][L*L][6][QyS]

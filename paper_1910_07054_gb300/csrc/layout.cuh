@@ -56,8 +56,11 @@ __host__ __device__ inline int tensor_row(int log2Py, bool fp64) {
     return (Qy + q - 1) / q * q;
 }
 
-// Floats per (kx, u) block of the u-major tensor layout: npairs * 6 padded to
-// 16 bytes so that every block starts on a 16-byte boundary.
-__host__ __device__ inline int umajor_block(int npairs) { return (npairs * 6 + 3) / 4 * 4; }
+// The u-major tensor layout (dense-product plans) holds one (kx, u) block of
+// 6 component rows, [component][pair]; each row is npairs padded to a multiple
+// of 4, so rows and blocks start on 16-byte boundaries.
+__host__ __device__ inline int umajor_row(int npairs) { return (npairs + 3) / 4 * 4; }
+// Floats per (kx, u) block.
+__host__ __device__ inline int umajor_block(int npairs) { return 6 * umajor_row(npairs); }
 
 }  // namespace demag

@@ -751,8 +751,8 @@ __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, in
     const double2 *base = planes + (size_t)P * 3 * Px * Py + (size_t)kq * Px + kx;
     const double2 A = base[0], Bp = base[(size_t)Px * Py], C = base[(size_t)2 * Px * Py];
     const double sc = 1.0 / ((double)Px * (double)Py);
-    const size_t cs = umajor ? 1 : QyS;  // component stride
-    T *o = umajor ? tensor + ((size_t)kx * Qy + u) * umajor_block(npairs) + (size_t)(p0 + P) * 6
+    const size_t cs = umajor ? (size_t)umajor_row(npairs) : QyS;  // component stride
+    T *o = umajor ? tensor + ((size_t)kx * Qy + u) * umajor_block(npairs) + (size_t)(p0 + P)
                   : tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * QyS + u;
     o[0 * cs] = (T)(A.x * sc);
     o[1 * cs] = (T)(A.y * sc);
