@@ -32,6 +32,31 @@ __device__ __forceinline__ void group_sync(int group) {
     asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(kGroup) : "memory");
 }
 
+// Programmatic dependent launch: the kernels below are launched so that they
+// may start while the previous kernel in the stream finishes.  Each waits for
+// that kernel (and its memory) before reading anything it may have written,
+// and lets its own successor be scheduled early.  Both are no-ops for a
+// normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Launch with programmatic stream serialization (see pdl_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Passes 2 and 3 of a forward or inverse transform held in shared memory
 // (input written by pass 1 at its destinations).  For INV with to_global, the
 // caller takes pass 3's outputs from `v` instead (positions j + 64 r).
@@ -415,6 +440,10 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
     // until the copy engine takes it, which must not stall a compute warp
     const bool producer = tid >= 512;
     if (producer && lane == 0) ring8_issue<L>(0, NS, ring, tk, full_row);
+    // the plan tensor and ratios above do not depend on the previous kernel;
+    // the spectrum does
+    pdl_wait();
+    pdl_release();
 
     const Bases8 bs(j);
     C w2[7], w3[7];
@@ -576,9 +605,29 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
 // Row transforms for Px = 512: 16 rows of one plane per 256-thread block, the
 // rows taken in pairs as one complex transform (z = row_a + i row_b), two
 // pairs per 64-thread group.  Same shared-memory layout as the column kernel
-// (one pad slot per 16) with an odd column stride, so the untangling step,
-// which reads eight columns at once, spreads over the banks as well.
-constexpr int kColRow = kN8 + kN8 / 16 + 1;
+// (one pad slot per 16); the column stride is 4 mod 16 words so that the
+// untangling step, where a warp reads 8 columns at 4 frequencies, spreads over
+// all banks.  Rows a and b of a pair are adjacent in the spectrum ([kx][y]), so
+// both are moved with one 16-byte access (ny even).
+constexpr int kColRow = kN8 + kN8 / 16 + 4;
+
+// Two consecutive complex values as one 16-byte access (16-byte aligned).
+__device__ __forceinline__ void store_pair(float2 *o, float2 a, float2 b) {
+    *reinterpret_cast<float4 *>(o) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store_pair(double2 *o, double2 a, double2 b) {
+    o[0] = a;
+    o[1] = b;
+}
+__device__ __forceinline__ void load_pair(const float2 *p, float2 &a, float2 &b) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const double2 *p, double2 &a, double2 &b) {
+    a = p[0];
+    b = p[1];
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
@@ -593,6 +642,8 @@ __global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
     const int plane = blockIdx.y, y0 = blockIdx.x * 16;
     const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
     const T *mp = m + (size_t)plane * ny * nx;
+    pdl_wait();
+    pdl_release();
     const T sc = layer_scale ? layer_scale[(plane / 3) % L] : (T)1;
     const Bases8 bs(j);
     // pass 1 straight from global memory (x = j + 64 r; zero for x >= nx and r >= 4)
@@ -626,26 +677,26 @@ __global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
     ring8_pass2<false, 2, kColRow, 4>(buf, group, 8, bs, w2, v);
     ring8_pass3<false, 2, kColRow, 4>(buf, group, 8, bs, w3, v, true);
     __syncthreads();
-    // A[k] = (Z[k] + conj Z[-k]) / 2,  B[k] = (Z[k] - conj Z[-k]) / (2i)
+    // A[k] = (Z[k] + conj Z[-k]) / 2,  B[k] = (Z[k] - conj Z[-k]) / (2i): one
+    // item per (kx, pair), rows a and b written together
     C *sp = spec + (size_t)plane * Kx * ny;
-    for (int e = threadIdx.x; e < Kx * 16; e += 256) {
-        const int kx = e >> 4, r = e & 15;
-        const int y = y0 + r;
-        if (y >= ny) continue;
-        const C *zb = buf + (r >> 1) * kColRow;
+    const bool pairs16 = (ny & 1) == 0;
+    for (int e = threadIdx.x; e < Kx * 8; e += 256) {
+        const int kx = e >> 3, q = e & 7;
+        const int ya = y0 + 2 * q;
+        if (ya >= ny) continue;
+        const C *zb = buf + q * kColRow;
         const C z1 = zb[pad16(kx)], z2 = zb[pad16((kN8 - kx) & (kN8 - 1))];
-        C o;
-        if ((r & 1) == 0)
-            o = C{(T)0.5 * (z1.x + z2.x), (T)0.5 * (z1.y - z2.y)};
-        else
-            o = C{(T)0.5 * (z1.y + z2.y), (T)0.5 * (z2.x - z1.x)};
-        sp[(size_t)kx * ny + y] = o;
+        const C a = C{(T)0.5 * (z1.x + z2.x), (T)0.5 * (z1.y - z2.y)};
+        const C b = C{(T)0.5 * (z1.y + z2.y), (T)0.5 * (z2.x - z1.x)};
+        C *o = sp + (size_t)kx * ny + ya;
+        if (pairs16 && ya + 1 < ny) {
+            store_pair(o, a, b);
+        } else {
+            o[0] = a;
+            if (ya + 1 < ny) o[1] = b;
+        }
     }
-}
-
-template <typename C>
-__device__ __forceinline__ C shfl_xor_c(C v, int mask) {
-    return C{__shfl_xor_sync(0xffffffffu, v.x, mask), __shfl_xor_sync(0xffffffffu, v.y, mask)};
 }
 
 template <typename T>
@@ -658,40 +709,52 @@ __global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>:
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);  // 8 row pairs x kColRow
     constexpr int half = kN8 / 2, Kx = half + 1;
-    constexpr int NIT = half * 16 / 256;  // spectrum entries per thread for kx < 256
     const int plane = blockIdx.y, y0 = blockIdx.x * 16;
     const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
     const C *sp = spec + (size_t)plane * Kx * ny;
+    pdl_wait();
+    pdl_release();
     const T scale = out_scale * (layer_scale ? layer_scale[(plane / 3) % L] : (T)1);
-    // thread (kx, r) reads row y0 + r at kx, coalesced (16 rows of one kx are
-    // contiguous); lanes r and r ^ 1 trade A (row a) and B (row b) of pair r / 2
-    const int r = threadIdx.x & 15, y = y0 + r;
-    C in[NIT];
+    // thread (kx, q) reads rows a and b of pair q at kx (adjacent, one 16-byte
+    // load) and writes Z[kx] = A + i B and Z[512 - kx] = conj(A) + i conj(B)
+    // of the pair's column; DC and Nyquist are real in A and B
+    const bool pairs16 = (ny & 1) == 0;
+    constexpr int NIT = half * 8 / 256;  // items per thread for kx < 256
+    const int qp = threadIdx.x & 7, ya = y0 + 2 * qp;
+    C av[NIT], bv[NIT];
 #pragma unroll
     for (int it = 0; it < NIT; ++it) {
-        const int kx = (threadIdx.x >> 4) + 16 * it;
-        in[it] = y < ny ? sp[(size_t)kx * ny + y] : C{0, 0};
+        const int kx = (threadIdx.x >> 3) + 32 * it;
+        const C *p = sp + (size_t)kx * ny + ya;
+        av[it] = C{0, 0};
+        bv[it] = C{0, 0};
+        if (ya + 1 < ny && pairs16) {
+            load_pair(p, av[it], bv[it]);
+        } else if (ya < ny) {
+            av[it] = p[0];
+            if (ya + 1 < ny) bv[it] = p[1];
+        }
     }
-    const C nyq = (threadIdx.x < 16 && y < ny) ? sp[(size_t)half * ny + y] : C{0, 0};
-    C *zb = buf + (r >> 1) * kColRow;
+    C *zb = buf + qp * kColRow;
 #pragma unroll
     for (int it = 0; it < NIT; ++it) {
-        const int kx = (threadIdx.x >> 4) + 16 * it;
-        const C other = shfl_xor_c(in[it], 1);
-        C A = (r & 1) ? other : in[it], B = (r & 1) ? in[it] : other;
+        const int kx = (threadIdx.x >> 3) + 32 * it;
+        C A = av[it], B = bv[it];
         if (kx == 0) {
             A.y = 0;
             B.y = 0;
-        }
-        // Z[kx] = A + i B, Z[512 - kx] = conj(A) + i conj(B)
-        if ((r & 1) == 0)
+            zb[pad16(0)] = C{A.x, B.x};
+        } else {
             zb[pad16(kx)] = C{A.x - B.y, A.y + B.x};
-        else if (kx != 0)
             zb[pad16(kN8 - kx)] = C{A.x + B.y, B.x - A.y};
+        }
     }
-    if (threadIdx.x < 32) {
-        const C other = shfl_xor_c(nyq, 1);
-        if (threadIdx.x < 16 && (r & 1) == 0) zb[pad16(half)] = C{nyq.x, other.x};  // A, B real at Nyquist
+    if (threadIdx.x < 8) {
+        const C *p = sp + (size_t)half * ny + ya;
+        C A = C{0, 0}, B = C{0, 0};
+        if (ya < ny) A = p[0];
+        if (ya + 1 < ny) B = p[1];
+        zb[pad16(half)] = C{A.x, B.x};  // A, B real at Nyquist
     }
     __syncthreads();
     // inverse transforms: pass 1 in shared memory, pass 3 straight to global
@@ -738,10 +801,8 @@ static cudaError_t launch_ring8(const ApplyArgs &a, cudaStream_t st) {
         cudaSuccess)
         return e;
     const int Kx = (1 << a.log2Px) / 2 + 1;
-    k_columns_ring8<L><<<dim3(Kx, a.B), 544, smem, st>>>((float2 *)a.spec, (const float *)a.tensor,
-                                                         (const float *)a.ratio, Kx, a.ny,
-                                                         (const float2 *)a.twy);
-    return cudaGetLastError();
+    return launch_pdl(k_columns_ring8<L>, dim3(Kx, a.B), dim3(544), smem, st, (float2 *)a.spec,
+                      (const float *)a.tensor, (const float *)a.ratio, Kx, a.ny, (const float2 *)a.twy);
 }
 
 // The streamed kernel takes float plans with L <= 8, the pair-symmetric
@@ -800,15 +861,16 @@ cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forw
         if ((e = cudaFuncSetAttribute(k_rows_forward8<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem)) != cudaSuccess)
             return e;
-        k_rows_forward8<T><<<grid, 256, smem, st>>>((const T *)m, (C *)a.spec, a.nx, a.ny,
-                                                    (const C *)a.twx, (const T *)a.in_scale, a.L);
+        if ((e = launch_pdl(k_rows_forward8<T>, grid, dim3(256), smem, st, (const T *)m, (C *)a.spec, a.nx,
+                            a.ny, (const C *)a.twx, (const T *)a.in_scale, a.L)) != cudaSuccess)
+            return e;
     } else {
         if ((e = cudaFuncSetAttribute(k_rows_inverse8<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem)) != cudaSuccess)
             return e;
-        k_rows_inverse8<T><<<grid, 256, smem, st>>>((const C *)a.spec, (T *)H, a.nx, a.ny,
-                                                    (const C *)a.twx, (T)(-a.Ms),
-                                                    (const T *)a.out_scale, a.L);
+        if ((e = launch_pdl(k_rows_inverse8<T>, grid, dim3(256), smem, st, (const C *)a.spec, (T *)H, a.nx,
+                            a.ny, (const C *)a.twx, (T)(-a.Ms), (const T *)a.out_scale, a.L)) != cudaSuccess)
+            return e;
     }
     return cudaGetLastError();
 }
