@@ -239,9 +239,12 @@ demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *
 /*
  * demag_apply_host - demag_apply on HOST buffers (end-to-end call).
  *
- * Copies m from host to the plan's device staging buffer, runs demag_apply,
- * copies H back to the host and synchronises the stream.  Host buffers should
- * be pinned (cudaHostAlloc) for full copy bandwidth; pageable memory works.
+ * With pinned (page-locked, device-mapped) m and H, the kernels read m from
+ * and write H to host memory directly over the host link, which overlaps the
+ * transfers with the row transforms; other host memory is copied through the
+ * plan's device staging buffers (allocated on first use) before and after
+ * demag_apply.  Either way the call synchronises the stream before it
+ * returns and the field is identical.
  *
  *   m, H   HOST, [B][L][3][ny][nx] of the plan's real type
  *   other arguments as in demag_apply

@@ -455,12 +455,26 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
     demag_status rc = check_apply(plan, m_host, Ms, H_host, B);
     if (rc != DEMAG_OK) return rc;
     const size_t bytes = plan->field_bytes_per_state * (size_t)B;
+    cudaStream_t st = (cudaStream_t)stream;
+    // pinned (page-locked, device-mapped) buffers: the kernels read m and write
+    // H in host memory directly, so the transfers overlap the row transforms
+    cudaPointerAttributes am, ah;
+    const bool direct = cudaPointerGetAttributes(&am, m_host) == cudaSuccess && am.type == cudaMemoryTypeHost &&
+                        am.devicePointer && cudaPointerGetAttributes(&ah, H_host) == cudaSuccess &&
+                        ah.type == cudaMemoryTypeHost && ah.devicePointer;
+    cudaGetLastError();  // attribute queries of unregistered memory may leave an error
+    if (direct) {
+        cudaError_t e = launch_apply(apply_args(plan, Ms, B), am.devicePointer, ah.devicePointer,
+                                     plan->precision == DEMAG_PREC_FP64, st);
+        if (e != cudaSuccess) return cuda_fail(e, "demag_apply_host kernels");
+        DEMAG_CUDA(cudaStreamSynchronize(st));
+        return DEMAG_OK;
+    }
     if (!plan->d_stage_m) {
         const size_t full = plan->field_bytes_per_state * (size_t)plan->max_batch;
         DEMAG_TRY(dalloc(&plan->d_stage_m, full, "host staging"));
         DEMAG_TRY(dalloc(&plan->d_stage_H, full, "host staging"));
     }
-    cudaStream_t st = (cudaStream_t)stream;
     DEMAG_CUDA(cudaMemcpyAsync(plan->d_stage_m, m_host, bytes, cudaMemcpyHostToDevice, st));
     cudaError_t e = launch_apply(apply_args(plan, Ms, B), plan->d_stage_m, plan->d_stage_H,
                                  plan->precision == DEMAG_PREC_FP64, st);

@@ -223,6 +223,24 @@ def test_host_entry_point_matches_device():
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP32, max_batch=2)
     mh = torch.tensor(m, dtype=torch.float32).pin_memory()
     Hh = torch.empty_like(mh).pin_memory()
+    dm.demag_apply_host(plan.handle, mh, 3.0, Hh)          # pinned: kernels access host memory
+    mp = torch.tensor(m, dtype=torch.float32)
+    Hp = torch.empty_like(mp)
+    dm.demag_apply_host(plan.handle, mp, 3.0, Hp)          # pageable: staged copies
+    Hd = plan.apply(mh.cuda(), 3.0).cpu()
+    plan.close()
+    assert torch.equal(Hh, Hd)
+    assert torch.equal(Hp, Hd)
+
+
+def test_host_entry_point_512_point_path():
+    """Pinned host buffers on the 512-point kernels (direct host access)."""
+    nx, ny, th = 200, 140, (1.0, 0.5, 2.0)
+    m = inputs.random_unit_vectors((1, len(th), ny, nx), seed=42)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP32)
+    assert plan.info["path"] == 5
+    mh = torch.tensor(m, dtype=torch.float32).pin_memory()
+    Hh = torch.empty_like(mh).pin_memory()
     dm.demag_apply_host(plan.handle, mh, 3.0, Hh)
     Hd = plan.apply(mh.cuda(), 3.0).cpu()
     plan.close()
