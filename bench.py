@@ -216,8 +216,9 @@ def run_reference(args):
 
 def batched_measurement(steps, peaks, n=512):
     """512 x 512 cells (n x n if given), 64 layers, 16 states per apply: the
-    split-precision tensor-core contraction (path 4) against the same products
-    on the FP32 cores (path 3), same plan, same data movement."""
+    split-precision contraction on the tcgen05 tensor cores (path 6, the plan's
+    default) and with warp-level MMAs (path 4), against the same products on
+    the FP32 cores (path 3); same plan, same data movement."""
     import numpy as np
     import torch
 
@@ -258,7 +259,7 @@ def batched_measurement(steps, peaks, n=512):
                           "frac": 3 * tc["contraction_tflops_useful"] / tf32_peak,
                           "note": "TF32 issue rate (3 passes per useful flop) against the measured bf16 "
                                   "burst peak x nominal tf32/bf16 ratio (1.1/2.25)"}
-    tc = out["tensor_cores_3xtf32"]
+    tc = out["tcgen05_3xtf32"]
     d = fields[4] - fields[3]
     out["rel_l2_between_variants"] = float(torch.linalg.vector_norm(d.double()) /
                                            torch.linalg.vector_norm(fields[3].double()))

@@ -169,18 +169,19 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
  *           first use).
  *   path 3: (DEMAG_PREC_SPLIT_TF32 plans) column kernels of path 2 with the
  *           contraction as dense L x L by L x B products on the FP32 cores.
- *   path 4: (DEMAG_PREC_SPLIT_TF32 plans, their default) the same products
- *           on the tensor cores in three TF32 passes (warp-level m16n8k8
- *           TF32 MMAs, two blocks per SM).
+ *   path 4: (DEMAG_PREC_SPLIT_TF32 plans) the same products on the tensor
+ *           cores in three TF32 passes (warp-level m16n8k8 TF32 MMAs, two
+ *           blocks per SM).
  *   path 5: (reported, not selectable otherwise) the fused column kernel with
  *           the radix-8 512-point transforms, chosen by demag_plan_create
  *           when Py = 512 and the columns fit; its tensor is stored in
  *           natural folded-ky order, so such a plan runs path 5 only.
- *   path 6: (DEMAG_PREC_SPLIT_TF32 plans, even L <= 64, max_batch <= 16) the
- *           same products on the tcgen05 tensor cores: 3xTF32, accumulators
- *           in tensor memory, one persistent block per SM.
+ *   path 6: (DEMAG_PREC_SPLIT_TF32 plans with even L <= 64 and max_batch <=
+ *           16, their default) the same products on the tcgen05 tensor cores:
+ *           3xTF32, the tensor operand built in tensor memory, accumulators in
+ *           tensor memory, one persistent block per SM.
  *   path 0: the default choice of demag_plan_create (5 or 1 when it fits,
- *           else 2; 4 for DEMAG_PREC_SPLIT_TF32).
+ *           else 2; for DEMAG_PREC_SPLIT_TF32 6 when it holds the plan, else 4).
  * All paths compute the same field (Eq. FFT_v2); this entry point exists to
  * test and time them against each other.  Errors: DEMAG_EINVAL, DEMAG_ENOMEM,
  * DEMAG_EUNSUPPORTED (the path cannot hold this plan).

@@ -307,7 +307,8 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
         }
         p->split = 1;
         p->umajor = 1;
-        p->contract_mode = 2;
+        // tcgen05 products where they hold the plan, else the warp-level MMAs
+        p->contract_mode = tc5_supported(L, max_batch, p->npairs) ? 3 : 2;
     } else {
         p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
         p->natural = !p->split && cols512_supported(p->log2Py, L, fp64) ? 1 : 0;

@@ -17,19 +17,29 @@
 // times t_j / t_i with xz and yz negated (reciprocity).  Products: a = a_hi +
 // a_lo, s = s_hi + s_lo (TF32), D += a_lo s_hi + a_hi s_lo + a_hi s_hi in FP32.
 //
-// One persistent block per SM walks the entries.  Roles:
+// One persistent block per SM walks the entries.  A lives in tensor memory:
+// each producer thread builds its own row of A (the thread's TMEM lane) for
+// 8 columns of K and stores them with tcgen05.st, so A is never staged in
+// shared memory; only S (N = 64 rows) passes through shared memory as the MMA's
+// B operand.  Roles:
 //   warp 21      loader: bulk copies of the entry's compact tensor and its two
 //                state rows (one copy per state, to a bank-spreading stride)
-//                into shared memory, and L2 prefetch two entries ahead;
-//   warps 0-15   producers: build A and S, hi and lo, from those copies,
-//                chunk by chunk of 16 columns of K (K-major canonical layout)
-//                into a 3-stage ring;
+//                into one of two input buffers, and L2 prefetch two entries
+//                ahead;
+//   warps 0-15   producers, chunk by chunk of 16 columns of K, 3 stages: a warp
+//                of lane quarter q (warp mod 4) builds hi and lo of the A rows in
+//                TMEM lanes 32 q + lane of one 128-row tile t, K columns
+//                8 h..8 h + 7, for one (t, h); warps without such a block build S
+//                (hi and lo, K-major canonical layout) in shared memory;
 //   warp 20      MMA issue (one thread; M = 128 row tiles, N = 64) and the
-//                tensor-memory allocation;
-//   warps 16-19  epilogue: accumulators (double-buffered in tensor memory) to
-//                the state rows.
-// Rows of the last 128-row tile beyond 3L read whatever shared memory follows
-// (the MMA needs 128 rows); those accumulator rows are never read.
+//                tensor-memory allocation (512 columns: accumulators
+//                double-buffered in 0..255, the A stages in 256..511);
+//   warps 16-19  epilogue: accumulators to the state rows.
+// Row r < 128 of A and D is lane r of tile 0; rows 128..3 Lp - 1 are the top
+// lanes of tile 1 (lane r - 128 + lane0 of tile 1, lane0 a multiple of 32), so
+// that the warps with two A blocks are in the upper lane quarters, away from
+// the MMA warp's scheduler.  Lanes that hold no row hold whatever tensor memory
+// held; they only feed accumulator rows that are never read.
 #include <cstdint>
 
 #include "internal.h"
@@ -41,18 +51,21 @@ namespace demag {
 namespace {
 
 constexpr int kTcProd = 16;                          // producer warps
-constexpr int kTcThreads = 32 * (kTcProd + 6);       // + 4 epilogue, MMA, prefetch warps
+constexpr int kTcThreads = 32 * (kTcProd + 6);       // + 4 epilogue, MMA, loader warps
 constexpr int kTcEpi = kTcProd, kTcMma = kTcProd + 4, kTcPre = kTcProd + 5;  // first warp of each role
 constexpr int kTcN = 64;         // accumulator columns: 2 positions x (re, im) x 16 states
 constexpr int kTcBp = 16;
 constexpr int kTcKC = 16;        // K columns per chunk (two MMA k-steps)
 constexpr int kTcStages = 3;
+constexpr int kTcCols = 512;     // tensor memory allocated
+constexpr int kTcAcol = 256;     // first column of the A stages
+constexpr int kTcAstage = 64;    // columns per A stage: 2 tiles x (16 hi + 16 lo)
 
 __device__ unsigned g_tc_timeouts;
 
 struct TcShape {
     int L, Lp, B, planes, R, T, nch, NB, seg;  // seg: padded float2 stride of one state's row segment
-    size_t raw_bytes, rows_bytes, a_bytes, s_bytes, stage_bytes, off_rows, off_stage, total;
+    size_t raw_bytes, rows_bytes, in_bytes, s_bytes, stage_bytes, off_stage, total;
 };
 
 __host__ __device__ inline size_t round128(size_t v) { return (v + 127) / 128 * 128; }
@@ -72,11 +85,10 @@ __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs) {
     s.seg = 3 * L + ((2 - (3 * L) % 16) + 16) % 16;
     s.raw_bytes = round128((size_t)s.NB * 4);
     s.rows_bytes = round128((size_t)2 * B * s.seg * 8);
-    s.a_bytes = (size_t)s.R * kTcKC * 4;
+    s.in_bytes = s.raw_bytes + s.rows_bytes;  // one input buffer (two of them)
     s.s_bytes = (size_t)kTcN * kTcKC * 4;
-    s.stage_bytes = round128(2 * s.a_bytes + 2 * s.s_bytes);
-    s.off_rows = s.raw_bytes;
-    s.off_stage = s.off_rows + s.rows_bytes;
+    s.stage_bytes = 2 * s.s_bytes;            // S hi, S lo
+    s.off_stage = 2 * s.in_bytes;
     s.total = s.off_stage + kTcStages * s.stage_bytes;
     return s;
 }
@@ -87,13 +99,41 @@ __device__ __forceinline__ int tc_comp(int co, int ci) {
     return t == 0 ? 0 : t == 4 ? 1 : t == 8 ? 2 : (t == 1 || t == 3) ? 3 : (t == 2 || t == 6) ? 4 : 5;
 }
 
-__device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
-    uint32_t h, l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-    const float r = v - __uint_as_float(h);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
-    hi = __uint_as_float(h);
-    lo = __uint_as_float(l);
+// Round a finite float to TF32 (10 explicit mantissa bits), to nearest with
+// ties away from zero: add half a unit of the last kept bit to the magnitude
+// bits and clear the 13 dropped ones (a carry into the exponent is the correct
+// result).  Two integer operations on the full-rate pipes.
+__device__ __forceinline__ uint32_t tf32_round(uint32_t bits) { return (bits + 0x1000u) & 0xFFFFE000u; }
+
+// v = hi + lo with hi the TF32 rounding of v and lo = v - hi exactly (|lo| <=
+// 2^-11 |v|).  lo goes to the tensor core as it is: a TF32 operand is read from
+// its upper 19 bits, so what reaches the product is lo truncated, within
+// 2^-10 |lo| <= 2^-21 |v| of it.
+__device__ __forceinline__ void split_tf32(float v, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_round(__float_as_uint(v));
+    lo = __float_as_uint(v - __uint_as_float(hi));
+}
+
+// One thread: the six MMAs of one 128-row tile and one 16-column chunk of K,
+// A from tensor memory (hi in columns at..at+15, lo in at+16..at+31), S hi and
+// lo from shared memory (descriptors bh, bl; +16 in the start-address field is
+// the second k-step, 256 bytes further):  D (+)= A_lo S_hi + A_hi S_lo + A_hi S_hi
+// for k-steps 0 and 1.  `accumulate` false starts D over.
+__device__ __forceinline__ void tc_mma_chunk(unsigned dt, unsigned at, uint64_t bh, uint64_t bl, uint32_t idesc,
+                                             bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred pa, pt;\n\t"
+        "setp.ne.b32 pa, %9, 0;\n\t"
+        "setp.eq.b32 pt, %9, %9;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%3], %5, %8, pa;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %6, %8, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %5, %8, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%4], %7, %8, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %10, %8, pt;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %7, %8, pt;\n\t}" ::"r"(dt),
+        "r"(at), "r"(at + 8), "r"(at + 16), "r"(at + 24), "l"(bh), "l"(bl), "l"(bh + 16), "r"(idesc),
+        "r"((unsigned)accumulate), "l"(bl + 16)
+        : "memory");
 }
 
 }  // namespace
@@ -104,16 +144,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                                                                int log2Px, int log2Py, int npairs) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t st_full[kTcStages], st_empty[kTcStages], d_full[2], d_empty[2];
-    __shared__ __align__(8) uint64_t in_full, in_empty;  // the entry's tensor and state rows in shared memory
+    __shared__ __align__(8) uint64_t in_full[2], in_empty[2];  // the entry's tensor and state rows
     __shared__ unsigned tmem_slot;
     __shared__ __align__(16) float s_tau[64], s_itau[64];
-    __shared__ int s_rb[64];  // index of pair (i, i) minus i: pair (i, j >= i) is s_rb[i] + j
+    __shared__ __align__(16) int s_rb[64];  // index of pair (i, i) minus i: pair (i, j >= i) is s_rb[i] + j
     __shared__ int s_abort;
     const TcShape sh = tc_shape(L, B, npairs);
     const int Py = 1 << log2Py, Qy = Py / 2 + 1, Kx = (1 << log2Px) / 2 + 1;
     const int nent = Kx * Qy;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Lp = sh.Lp, planes = sh.planes, R = sh.R;
+    const int lane0 = 128 - (R > 128 ? (R - 128 + 31) / 32 * 32 : 0);  // first TMEM lane of tile 1's rows
     bool ok = true;
 
     if (tid == 0) {
@@ -124,9 +165,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         for (int k = 0; k < 2; ++k) {
             mbar_init(&d_full[k], 1);
             mbar_init(&d_empty[k], 4);
+            mbar_init(&in_full[k], 1);
+            mbar_init(&in_empty[k], kTcProd);
         }
-        mbar_init(&in_full, 1);
-        mbar_init(&in_empty, kTcProd);
         mbar_init_fence();
         s_abort = 0;
     }
@@ -135,7 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         s_itau[tid] = tid < L ? ratio[tid * L] : 0.f;  // t_0 / t_l
         s_rb[tid] = tid * L - (tid * (tid - 1)) / 2 - tid;
     }
-    if (warp == kTcMma) tc_alloc(&tmem_slot, 256);
+    if (warp == kTcMma) tc_alloc(&tmem_slot, kTcCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -145,160 +186,235 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         const int f = blockIdx.x + lf * gridDim.x;
         kx = f / Qy;
         u = f - kx * Qy;
-        u_positions(u, log2Py, p1, p2);
+        // positions of stored entry u (the order of u_positions, with bit intrinsics)
+        if (u < 2) {
+            p1 = p2 = u;
+        } else {
+            const int m = 32 - __clz(u - 1);  // u - 1 in [2^(m-1), 2^m)
+            const int rr = u - (1 << (m - 1)) - 1;
+            p1 = (1 << m) + rr;
+            p2 = (2 << m) - 1 - rr;
+        }
         npos = p2 != p1 ? 2 : 1;
-        mir0 = bitrev_n(p1, log2Py) > Py / 2;  // position 0 is the mirrored frequency
+        mir0 = (int)(__brev((unsigned)p1) >> (32 - log2Py)) > Py / 2;  // position 0 is the mirrored frequency
     };
     const int nlocal = blockIdx.x < nent ? (nent - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == kTcPre) {
-        // loader: entry lf into shared memory once the producers released lf - 1;
-        // L2 prefetch of entry lf + 2
-        if (lane == 0) {
-            auto prefetch = [&](int lf) {
-                if (lf >= nlocal) return;
-                int kx, u, p1, p2, npos;
-                bool mir0;
-                entry(lf, kx, u, p1, p2, npos, mir0);
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tensor_um + ((size_t)kx * Qy + u) * sh.NB),
-                             "r"((unsigned)sh.NB * 4) : "memory");
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(spec2 + ((size_t)kx * Py + p1) * planes),
+        // loader: entry lf into buffer lf mod 2 once the producers released
+        // entry lf - 2 (lane 0 waits and announces the bytes; the per-state
+        // copies are issued by all lanes, one each); L2 prefetch of entry lf + 2
+        auto prefetch = [&](int lf) {
+            if (lf >= nlocal) return;
+            int kx, u, p1, p2, npos;
+            bool mir0;
+            entry(lf, kx, u, p1, p2, npos, mir0);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tensor_um + ((size_t)kx * Qy + u) * sh.NB),
+                         "r"((unsigned)sh.NB * 4) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(spec2 + ((size_t)kx * Py + p1) * planes),
+                         "r"((unsigned)planes * 8) : "memory");
+            if (npos == 2)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                                 spec2 + ((size_t)kx * Py + p2) * planes),
                              "r"((unsigned)planes * 8) : "memory");
-                if (npos == 2)
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
-                                     spec2 + ((size_t)kx * Py + p2) * planes),
-                                 "r"((unsigned)planes * 8) : "memory");
-            };
+        };
+        if (lane == 0) {
             prefetch(0);
             prefetch(1);
-            const unsigned segb = (unsigned)(3 * L) * 8;  // one state's values (16-byte multiple)
-            for (int lf = 0; lf < nlocal && ok; ++lf) {
-                if (lf >= 1 && !mbar_wait(&in_empty, (lf - 1) & 1, &g_tc_timeouts)) ok = false;
-                int kx, u, p1, p2, npos;
-                bool mir0;
-                entry(lf, kx, u, p1, p2, npos, mir0);
-                mbar_arrive_expect_tx(&in_full, (unsigned)sh.NB * 4 + (unsigned)(npos * B) * segb);
-                bulk_copy_g2s(smem, tensor_um + ((size_t)kx * Qy + u) * sh.NB, (unsigned)sh.NB * 4, &in_full);
-                for (int q = 0; q < npos; ++q) {
-                    const float2 *src = spec2 + ((size_t)kx * Py + (q ? p2 : p1)) * planes;
-                    float2 *dst = reinterpret_cast<float2 *>(smem + sh.off_rows) + (size_t)q * B * sh.seg;
-                    for (int b = 0; b < B; ++b)
-                        bulk_copy_g2s(dst + (size_t)b * sh.seg, src + (size_t)b * 3 * L, segb, &in_full);
-                }
-                prefetch(lf + 2);
+        }
+        const unsigned segb = (unsigned)(3 * L) * 8;  // one state's values (16-byte multiple)
+        for (int lf = 0; lf < nlocal && ok; ++lf) {
+            const int buf = lf & 1;
+            if (lane == 0 && lf >= 2 && !mbar_wait(&in_empty[buf], ((lf >> 1) - 1) & 1, &g_tc_timeouts)) ok = false;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            int kx, u, p1, p2, npos;
+            bool mir0;
+            entry(lf, kx, u, p1, p2, npos, mir0);
+            unsigned char *in = smem + (size_t)buf * sh.in_bytes;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&in_full[buf], (unsigned)sh.NB * 4 + (unsigned)(npos * B) * segb);
+                bulk_copy_g2s(in, tensor_um + ((size_t)kx * Qy + u) * sh.NB, (unsigned)sh.NB * 4, &in_full[buf]);
             }
+            __syncwarp();
+            for (int c = lane; c < npos * B; c += 32) {
+                const int q = c >= B, b = c - q * B;
+                const float2 *src = spec2 + ((size_t)kx * Py + (q ? p2 : p1)) * planes + (size_t)b * 3 * L;
+                float2 *dst = reinterpret_cast<float2 *>(in + sh.raw_bytes) + ((size_t)q * B + b) * sh.seg;
+                bulk_copy_g2s(dst, src, segb, &in_full[buf]);
+            }
+            if (lane == 0) prefetch(lf + 2);
         }
     } else if (warp < kTcProd) {
-        // producers: a unit is 4 consecutive K columns of one row (16 bytes of one
-        // core-matrix row); 8 consecutive units fill one core matrix, so each warp
-        // store covers whole 128-byte core matrices.  A thread keeps its units (and
-        // everything about them that does not depend on the chunk) for the whole run.
-        constexpr int KG = kTcKC / 4;  // core matrices along K per chunk
-        constexpr int NU = 4;          // at most 4 units per thread and chunk
-        const int na = R * KG, ntot = na + kTcN * KG;
-        const float *raw = reinterpret_cast<const float *>(smem);  // [6][NR]
-        const float2 *rows = reinterpret_cast<const float2 *>(smem + sh.off_rows);
-        const int NR = umajor_row(npairs);
-        struct Unit {
-            int off;      // float offset in the A or S buffer of a stage
-            int row, k4;  // row (A: co * Lp + i; S: column n), core column
-            int c0, c1, c2;  // A: stored component for source component x, y, z
-            bool isA, live;
+        // producers.  Warp (q = warp mod 4, wq = warp / 4): A block wq of lane
+        // quarter q if that quarter has wq < nA(q) blocks (two K halves per
+        // 128-row tile that has rows in the quarter), else S worker.
+        const int q = warp & 3, wq = warp >> 2;
+        auto nA = [&](int qq) {
+            const bool t0 = 32 * qq < R;
+            const bool t1 = 32 * qq + 32 > lane0 && 32 * qq < lane0 + (R - 128);
+            return 2 * ((int)t0 + (int)t1);
         };
-        Unit un[NU];
-#pragma unroll
-        for (int k = 0; k < NU; ++k) {
-            const int v = tid + k * 32 * kTcProd;
-            Unit &x = un[k];
-            x.live = v < ntot;
-            x.isA = v < na;
-            const int w = x.isA ? v : v - na;
-            const int core = w >> 3, rr = w & 7;
-            x.row = (core / KG) * 8 + rr;
-            x.k4 = core % KG;
-            x.off = core * 32 + rr * 4;
-            const int co = (x.row >= Lp) + (x.row >= 2 * Lp);
-            x.c0 = tc_comp(co, 0);
-            x.c1 = tc_comp(co, 1);
-            x.c2 = tc_comp(co, 2);
+        const bool isA = wq < nA(q);
+        int sidx = 0, nS = 0;
+        for (int w = 0; w < kTcProd; ++w) {
+            const bool s_w = (w >> 2) >= nA(w & 3);
+            if (s_w && w < warp) ++sidx;
+            nS += s_w;
         }
+        const int NR = umajor_row(npairs);
+        // All shared-memory operands below are byte offsets from smem (32-bit
+        // shared-window addressing).
+        // A block: row r of A (co, i), K columns 8 h .. 8 h + 7 of each chunk.
+        // Lanes without a row (r >= 3 Lp or i >= L) read pair (0, j), which
+        // exists, with scale 0.
+        const int t = (wq >> 1) > 0 || 32 * q >= R, h = wq & 1;  // a quarter without tile-0 rows has tile 1 only
+        const int r = t == 0 ? 32 * q + lane : 128 + 32 * q + lane - lane0;
+        const int cor = r / Lp;
+        const bool rvalid = isA && r < R && r - cor * Lp < L;
+        const int co = rvalid ? cor : 0, i = rvalid ? r - cor * Lp : 0;
+        const float vs = rvalid ? 1.f : 0.f;
+        const int srb_i = s_rb[i];
+        const float itau_i = s_itau[i];
+        const unsigned ta_row = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(kTcAcol + 32 * t + 8 * h);
+        // per source component ci: byte offset of the stored component row, and
+        // the scale of the upper (j >= i, stored pair (i, j)) and lower (j < i,
+        // stored pair (j, i) times t_j / t_i, xz and yz negated) triangles
+        int offc[3];
+        float sup[3], slo[3];
+#pragma unroll
+        for (int ci = 0; ci < 3; ++ci) {
+            const int comp = tc_comp(co, ci);
+            const float zs = (co == 2 && ci == 2) ? -vs : vs;
+            offc[ci] = comp * NR * 4;
+            sup[ci] = zs;
+            slo[ci] = zs * itau_i * (comp >= 4 ? -1.f : 1.f);
+        }
+        // S unit of this thread: (position pq, state b, core column k4)
+        constexpr int KG = kTcKC / 4;
+        const int sv = lane + 32 * sidx;
+        const bool sact = !isA && sv < 2 * kTcBp * KG;
+        const int k4 = sv & (KG - 1), sb = (sv >> 2) & (kTcBp - 1), spq = (sv >> 6) & 1;
+        const int sn = 32 * spq + sb;  // real column of S; the imaginary one is sn + 16
+        const int soff_r = (((sn >> 3) * KG + k4) * 32 + (sn & 7) * 4) * 4;
+        const int soff_i = soff_r + 2 * KG * 32 * 4;  // 16 rows = two 8-row groups further
+        const int srow = (int)sh.raw_bytes + (spq * B + sb) * sh.seg * 8;
+
         for (int lf = 0; lf < nlocal && ok; ++lf) {
             int kx, u, p1, p2, npos;
             bool mir0;
             entry(lf, kx, u, p1, p2, npos, mir0);
-            if (!mbar_wait(&in_full, lf & 1, &g_tc_timeouts)) ok = false;
+            const int buf = lf & 1;
+            if (!mbar_wait(&in_full[buf], (lf >> 1) & 1, &g_tc_timeouts)) ok = false;
+            const int inb = buf * (int)sh.in_bytes;  // this entry's input buffer
+            const bool slive = sact && spq < npos && sb < B;
+            const float sy0 = ((spq == 0) == mir0) ? -1.f : 1.f;  // m_y negated at the mirrored position
             for (int ch = 0; ch < sh.nch && ok; ++ch) {
                 const int gch = lf * sh.nch + ch, s = gch % kTcStages, use = gch / kTcStages;
                 if (use >= 1 && !mbar_wait(&st_empty[s], (use - 1) & 1, &g_tc_timeouts)) ok = false;
-                float *a_hi = reinterpret_cast<float *>(smem + sh.off_stage + s * sh.stage_bytes);
-                float *a_lo = a_hi + R * kTcKC, *s_hi = a_lo + R * kTcKC, *s_lo = s_hi + kTcN * kTcKC;
+                tc_fence_after();
+                if (isA) {
+                    const int kc0 = ch * kTcKC + 8 * h;  // first K column of the block
+                    uint32_t hi[8], lo[8];
+                    if (kc0 < R) {
+                        const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), jb = kc0 - ci * Lp;
+                        const int off = inb + (ci == 0 ? offc[0] : (ci == 1 ? offc[1] : offc[2]));
+                        const float su = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
+                        const float sl = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
+                        const int bu = off + (srb_i + jb) * 4;  // + 4 e: pair (i, jb + e)
+                        const int bl = off + i * 4;             // + 4 s_rb[j]: pair (j, i)
+                        const int4 rb0 = *reinterpret_cast<const int4 *>(s_rb + jb);
+                        const int4 rb1 = *reinterpret_cast<const int4 *>(s_rb + jb + 4);
+                        const float4 tj0 = *reinterpret_cast<const float4 *>(s_tau + jb);
+                        const float4 tj1 = *reinterpret_cast<const float4 *>(s_tau + jb + 4);
+                        const int rbj[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+                        const float tj[8] = {tj0.x, tj0.y, tj0.z, tj0.w, tj1.x, tj1.y, tj1.z, tj1.w};
+                        const int d = i - jb;  // column e is in the upper triangle iff e >= d
+                        if (jb + 8 <= L) {
 #pragma unroll
-                for (int k = 0; k < NU; ++k) {
-                    const Unit &x = un[k];
-                    if (!x.live) continue;
-                    const int kc = ch * kTcKC + 4 * x.k4;  // first K column of the unit
-                    const int ci = (kc >= Lp) + (kc >= 2 * Lp), jb = kc - ci * Lp;
-                    float val[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (kc < R) {
-                        if (x.isA) {
-                            const int co = (x.row >= Lp) + (x.row >= 2 * Lp), i = x.row - co * Lp;
-                            const int comp = ci == 0 ? x.c0 : (ci == 1 ? x.c1 : x.c2);
-                            const float zs = (co == 2 && ci == 2) ? -1.f : 1.f;
-                            if (i < L) {
-                                if (jb >= i) {
-                                    // upper triangle: pairs (i, jb..jb+3) are consecutive
-                                    const float *pb = raw + comp * NR + s_rb[i] + jb;
-#pragma unroll
-                                    for (int e = 0; e < 4; ++e)
-                                        if (jb + e < L) val[e] = zs * pb[e];
-                                } else {
-                                    const float4 tj = *reinterpret_cast<const float4 *>(s_tau + jb);
-                                    const float tjs[4] = {tj.x, tj.y, tj.z, tj.w};
-                                    const float sc = zs * s_itau[i] * (comp >= 4 ? -1.f : 1.f);
-#pragma unroll
-                                    for (int e = 0; e < 4; ++e) {
-                                        const int j = jb + e;
-                                        if (j >= L) continue;
-                                        val[e] = j < i ? sc * tjs[e] * raw[comp * NR + s_rb[j] + i]
-                                                       : zs * raw[comp * NR + s_rb[i] + j];
-                                    }
-                                }
+                            for (int e = 0; e < 8; ++e) {
+                                const bool up = e >= d;
+                                const int a = up ? bu + 4 * e : bl + 4 * rbj[e];
+                                const float sc = up ? su : sl * tj[e];
+                                split_tf32(sc * *reinterpret_cast<const float *>(smem + a), hi[e], lo[e]);
                             }
                         } else {
-                            const int q = x.row >> 5, ri = (x.row >> 4) & 1, b = x.row & (kTcBp - 1);
-                            if (q < npos && b < B) {
-                                const bool neg_y = (ci == 1) && ((q == 0) == mir0);
-                                const float2 *m = rows + ((size_t)q * B + b) * sh.seg + jb * 3 + ci;
+                            // last block of a component: columns j >= L are zero
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    if (jb + e >= L) continue;
-                                    const float2 mv = m[3 * e];
-                                    const float xv = ci < 2 ? (ri ? mv.y : mv.x) : (ri ? mv.x : -mv.y);
-                                    val[e] = neg_y ? -xv : xv;
-                                }
+                            for (int e = 0; e < 8; ++e) {
+                                const bool in = jb + e < L, up = e >= d;
+                                const int a = !in ? off : (up ? bu + 4 * e : bl + 4 * rbj[e]);
+                                const float sc = !in ? 0.f : (up ? su : sl * tj[e]);
+                                split_tf32(sc * *reinterpret_cast<const float *>(smem + a), hi[e], lo[e]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) hi[e] = lo[e] = 0u;
+                    }
+                    const unsigned ta = ta_row + (unsigned)(s * kTcAstage);
+                    tc_st8(ta, hi);
+                    tc_st8(ta + 16, lo);
+                    tc_wait_st();
+                } else if (sact) {
+                    // S unit: one (position, state) and 4 consecutive K columns; the
+                    // 4 complex values give 16 bytes of the core-matrix rows of both
+                    // its columns of S: rows x, y take (Re, Im), rows z (-Im, Re)
+                    const int kc = ch * kTcKC + 4 * k4;
+                    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (slive && kc < R) {
+                        const int ci = (kc >= Lp) + (kc >= 2 * Lp), jb = kc - ci * Lp;
+                        const bool z = ci == 2;
+                        const float sre = z ? -1.f : (ci == 1 ? sy0 : 1.f);
+                        const float sim = z ? 1.f : (ci == 1 ? sy0 : 1.f);
+                        const int a = inb + srow + (jb * 3 + ci) * 8;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (jb + e < L) {
+                                const float2 mv = *reinterpret_cast<const float2 *>(smem + a + 24 * e);
+                                re[e] = sre * (z ? mv.y : mv.x);
+                                im[e] = sim * (z ? mv.x : mv.y);
                             }
                         }
                     }
-                    float4 h, l;
-                    split_tf32(val[0], h.x, l.x);
-                    split_tf32(val[1], h.y, l.y);
-                    split_tf32(val[2], h.z, l.z);
-                    split_tf32(val[3], h.w, l.w);
-                    *reinterpret_cast<float4 *>((x.isA ? a_hi : s_hi) + x.off) = h;
-                    *reinterpret_cast<float4 *>((x.isA ? a_lo : s_lo) + x.off) = l;
+                    uint4 hr, lr, hm, lm;
+                    split_tf32(re[0], hr.x, lr.x);
+                    split_tf32(re[1], hr.y, lr.y);
+                    split_tf32(re[2], hr.z, lr.z);
+                    split_tf32(re[3], hr.w, lr.w);
+                    split_tf32(im[0], hm.x, lm.x);
+                    split_tf32(im[1], hm.y, lm.y);
+                    split_tf32(im[2], hm.z, lm.z);
+                    split_tf32(im[3], hm.w, lm.w);
+                    unsigned char *st_hi = smem + sh.off_stage + s * sh.stage_bytes;
+                    unsigned char *st_lo = st_hi + sh.s_bytes;
+                    *reinterpret_cast<uint4 *>(st_hi + soff_r) = hr;
+                    *reinterpret_cast<uint4 *>(st_lo + soff_r) = lr;
+                    *reinterpret_cast<uint4 *>(st_hi + soff_i) = hm;
+                    *reinterpret_cast<uint4 *>(st_lo + soff_i) = lm;
                 }
-                fence_proxy_async_smem();
+                if (!isA) fence_proxy_async_smem();
+                tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&st_full[s]);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&in_empty);  // the entry's inputs are no longer read
+            if (lane == 0) mbar_arrive(&in_empty[buf]);  // the entry's inputs are no longer read
         }
     } else if (warp == kTcMma) {
         // MMA issue
         if (lane == 0) {
             const uint32_t idesc = tc_idesc_tf32(128, kTcN);
             constexpr unsigned LBO = 128, SBO = (kTcKC / 4) * 128;  // K-adjacent cores; 8-row groups
+            // S descriptors of each stage; one k-step (8 K columns = two core
+            // matrices, 256 bytes) further is +16 in the start-address field
+            uint64_t dhi[kTcStages], dlo[kTcStages];
+#pragma unroll
+            for (int k = 0; k < kTcStages; ++k) {
+                const unsigned a = smem_addr(smem + sh.off_stage + k * sh.stage_bytes);
+                dhi[k] = tc_smem_desc(a, LBO, SBO);
+                dlo[k] = tc_smem_desc(a + (unsigned)sh.s_bytes, LBO, SBO);
+            }
             for (int lf = 0; lf < nlocal && ok; ++lf) {
                 const int db = lf & 1;
                 if (lf >= 2 && !mbar_wait(&d_empty[db], ((lf >> 1) - 1) & 1, &g_tc_timeouts)) ok = false;
@@ -307,22 +423,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                     const int gch = lf * sh.nch + ch, s = gch % kTcStages, use = gch / kTcStages;
                     if (!mbar_wait(&st_full[s], use & 1, &g_tc_timeouts)) ok = false;
                     tc_fence_after();
-                    const unsigned stage = smem_addr(smem + sh.off_stage + s * sh.stage_bytes);
-                    const unsigned a_hi = stage, a_lo = stage + (unsigned)sh.a_bytes;
-                    const unsigned s_hi = a_lo + (unsigned)sh.a_bytes, s_lo = s_hi + (unsigned)sh.s_bytes;
+                    const uint64_t bh = s == 0 ? dhi[0] : (s == 1 ? dhi[1] : dhi[2]);
+                    const uint64_t bl = s == 0 ? dlo[0] : (s == 1 ? dlo[1] : dlo[2]);
                     for (int t = 0; t < sh.T; ++t) {
                         const unsigned dt = tmem + (unsigned)((db * sh.T + t) * kTcN);
-                        const unsigned toff = (unsigned)t * 16 * SBO;  // 128 rows further
-#pragma unroll
-                        for (int ks = 0; ks < kTcKC / 8; ++ks) {
-                            const unsigned ko = (unsigned)ks * 2 * LBO;  // 8 K columns further
-                            tc_mma_tf32(dt, tc_smem_desc(a_lo + toff + ko, LBO, SBO),
-                                        tc_smem_desc(s_hi + ko, LBO, SBO), idesc, ch > 0 || ks > 0);
-                            tc_mma_tf32(dt, tc_smem_desc(a_hi + toff + ko, LBO, SBO),
-                                        tc_smem_desc(s_lo + ko, LBO, SBO), idesc, true);
-                            tc_mma_tf32(dt, tc_smem_desc(a_hi + toff + ko, LBO, SBO),
-                                        tc_smem_desc(s_hi + ko, LBO, SBO), idesc, true);
-                        }
+                        const unsigned at = tmem + (unsigned)(kTcAcol + s * kTcAstage + 32 * t);
+                        tc_mma_chunk(dt, at, bh, bl, idesc, ch > 0);
                     }
                     tc_commit(&st_empty[s]);
                 }
@@ -340,35 +446,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
             bool mir0;
             entry(lf, kx, u, p1, p2, npos, mir0);
             for (int t = 0; t < sh.T; ++t) {
-                const int rg = t * 128 + 32 * ew + lane;
-                const int co = rg / Lp, i = rg - co * Lp;
+                const int tl = 32 * ew + lane;  // TMEM lane
+                const bool lane_row = t == 0 || tl >= lane0;
+                const int rg = t == 0 ? tl : 128 + tl - lane0;
+                const int cog = rg / Lp, ig = rg - cog * Lp;
                 // one position (32 columns: 16 real, 16 imaginary) at a time
-                for (int q = 0; q < 2; ++q) {
-                    uint32_t r[32];
+                for (int pq = 0; pq < 2; ++pq) {
+                    uint32_t rr[32];
                     const unsigned ta = tmem + ((unsigned)(32 * ew) << 16) +
-                                        (unsigned)((db * sh.T + t) * kTcN + 32 * q);
-                    tc_ld32(ta, r);
+                                        (unsigned)((db * sh.T + t) * kTcN + 32 * pq);
+                    tc_ld32(ta, rr);
                     tc_wait_ld();
-                    if (t == sh.T - 1 && q == 1) {
+                    if (t == sh.T - 1 && pq == 1) {
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&d_empty[db]);
                     }
-                    if (q >= npos || rg >= R || i >= L) continue;
-                    const bool mir = (q == 0) == mir0;
-                    float2 *dst = spec2 + ((size_t)kx * Py + (q ? p2 : p1)) * planes + i * 3 + co;
+                    if (!lane_row || pq >= npos || rg >= R || ig >= L) continue;
+                    const bool mir = (pq == 0) == mir0;
+                    float2 *dst = spec2 + ((size_t)kx * Py + (pq ? p2 : p1)) * planes + ig * 3 + cog;
 #pragma unroll
                     for (int b = 0; b < kTcBp; ++b) {
                         if (b >= B) break;
-                        const float dre = __uint_as_float(r[b]), dim = __uint_as_float(r[16 + b]);
-                        float2 h;
-                        if (co == 2)
-                            h = make_float2(-dim, dre);
-                        else if (co == 1 && mir)
-                            h = make_float2(-dre, -dim);
+                        const float dre = __uint_as_float(rr[b]), dim = __uint_as_float(rr[16 + b]);
+                        float2 hh;
+                        if (cog == 2)
+                            hh = make_float2(-dim, dre);
+                        else if (cog == 1 && mir)
+                            hh = make_float2(-dre, -dim);
                         else
-                            h = make_float2(dre, dim);
-                        dst[(size_t)b * 3 * L] = h;
+                            hh = make_float2(dre, dim);
+                        dst[(size_t)b * 3 * L] = hh;
                     }
                 }
             }
@@ -384,7 +492,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         }
         __syncwarp();
         tc_fence_after();
-        tc_dealloc(tmem, 256);
+        tc_dealloc(tmem, kTcCols);
     }
 }
 

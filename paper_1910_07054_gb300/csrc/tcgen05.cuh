@@ -1,6 +1,7 @@
 // Fifth-generation tensor core (tcgen05) wrappers: tensor-memory allocation,
-// shared-memory operand descriptors, the kind::tf32 MMA, completion through an
-// mbarrier, and accumulator reads.
+// shared-memory operand descriptors, the kind::tf32 MMA (A from shared or from
+// tensor memory), completion through an mbarrier, tensor-memory stores and
+// accumulator reads.
 //
 // Operands sit in shared memory in the K-major, unswizzled canonical layout:
 // core matrices of 8 rows x 16 bytes (8 x 4 tf32), each 128 contiguous bytes;
@@ -64,6 +65,29 @@ __device__ __forceinline__ void tc_mma_tf32(unsigned dtmem, uint64_t adesc, uint
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"((unsigned)accumulate)
         : "memory");
 }
+
+// One thread: D[tmem] (+)= A[a_tmem] * B[bdesc], A read from tensor memory (row r
+// of an M = 128 operand in lane r, K element k of the instruction in column
+// a_tmem + k, one 32-bit tf32 value per column).
+__device__ __forceinline__ void tc_mma_tf32_ta(unsigned dtmem, unsigned atmem, uint64_t bdesc, uint32_t idesc,
+                                               bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dtmem),
+        "r"(atmem), "l"(bdesc), "r"(idesc), "r"((unsigned)accumulate)
+        : "memory");
+}
+
+// Whole warp: lane t writes 8 consecutive 32-bit columns of TMEM lane
+// (lane base of taddr + t); the lane base is the warp's own quarter.
+__device__ __forceinline__ void tc_st8(unsigned taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+// Whole warp: this thread's tcgen05.st writes have completed.
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // One thread: arrive once on `bar` when all tcgen05 operations it issued so far
 // have completed.

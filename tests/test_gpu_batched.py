@@ -1,9 +1,10 @@
 """GPU parity of the batched, many-layer contraction (DEMAG_PREC_SPLIT_TF32):
-the dense-product contraction on the tensor cores (three TF32 passes, path 4)
-and the same products on the FP32 cores (path 3), against the oracle.
+the dense-product contraction on the tcgen05 tensor cores (three TF32 passes,
+path 6), with warp-level MMAs (path 4) and the same products on the FP32 cores
+(path 3), against the oracle.
 
-Tolerance: 1e-5 relative L2 against the float64 oracle for both (the
-library's float32 target); the two variants within 3e-6 of each other.
+Tolerance: 1e-5 relative L2 against the float64 oracle for all (the
+library's float32 target); the variants within 3e-6 of each other.
 """
 import numpy as np
 import pytest
@@ -48,8 +49,9 @@ def _fields(plan, m, Ms, paths):
 def test_split_tf32_matches_oracle(nx, ny, th, B):
     m = inputs.random_unit_vectors((B, len(th), ny, nx), seed=len(th) + B)
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
-    assert plan.info["path"] == 4
-    paths = (4, 3, 6) if len(th) % 2 == 0 else (4, 3)  # path 6: tcgen05, even L
+    even = len(th) % 2 == 0
+    assert plan.info["path"] == (6 if even else 4)  # tcgen05 (path 6) wherever it holds the plan
+    paths = (4, 3, 6) if even else (4, 3)
     H = _fields(plan, m, 8e5, paths)
     plan.close()
     assert dm.demag_wait_timeouts() == 0
@@ -80,3 +82,25 @@ def test_scale512_batch_sampled_against_oracle():
                              m[state], inputs.MS_DEFAULT, [target])[target]
     assert rel_l2(H[4][state, target], ref) < 1e-5
     assert rel_l2(H[3][state, target], ref) < 1e-5
+    assert rel_l2(H[6][state, target], ref) < 1e-5
+
+
+@pytest.mark.parametrize("path", [3, 4, 6])
+def test_split_tf32_adjoint_matches_oracle(path):
+    """The adjoint (transposed-block convolution) through the dense-product
+    contraction: sources scaled by 1/t_j and targets by t_i around the same
+    products."""
+    nx, ny, th, B = 13, 9, (1.0, 0.5, 2.0, 0.8), 3
+    g = inputs.random_unit_vectors((B, len(th), ny, nx), seed=31)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    dm.demag_plan_set_path(plan.handle, path)
+    info = dm.demag_plan_info(plan.handle)
+    gt = torch.tensor(g, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(gt)
+    dm.demag_apply_adjoint(plan.handle, gt, 3.0, out, info=info)
+    torch.cuda.synchronize()
+    plan.close()
+    assert dm.demag_wait_timeouts() == 0
+    K = reading_kernels(nx, ny, 2.0, 2.0, th)
+    KT = np.transpose(K[:, :, :, ::-1, ::-1], (1, 0, 2, 3, 4))  # KT[i, j](d) = K[j, i](-d)
+    assert rel_l2(out.double().cpu().numpy(), odm.hybrid(KT, g, 3.0)) < 1e-5
