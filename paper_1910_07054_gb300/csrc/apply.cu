@@ -19,6 +19,8 @@
 //   k_rows_inverse  complex-to-real inverse FFT along x, cropped to nx and
 //                   scaled by -Ms (the 1/(Px Py) of the inverse DFT is folded
 //                   into the stored tensor).
+// Float rows of Px = 512 and 1024 use the radix-8 kernels of apply512.cu and
+// rows1024.cu instead of k_rows_forward / k_rows_inverse.
 #include "fft.cuh"
 #include "internal.h"
 #include "layout.cuh"
@@ -336,9 +338,12 @@ static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t
     if (e != cudaSuccess) return e;
     dim3 grid_rows(chunks, planes);
     const bool rows512 = a.log2Px == 9;
+    const bool rows1024 = rows1024_supported(a.log2Px, a.nx, sizeof(T) == 8);
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
     if (rows512)
         e = launch_rows512<T>(a, m, H, true, st);
+    else if (rows1024)
+        e = launch_rows1024(false, m, a.spec, a.nx, a.ny, planes, a.twx, a.log2twx, 0.f, a.in_scale, a.L, st);
     else {
         k_rows_forward<T><<<grid_rows, kRowThreads, smem_rows, st>>>(m, (C *)a.spec, a.nx, a.ny, a.log2Px,
                                                                      npair, (const C *)a.twx, a.log2twx,
@@ -353,6 +358,9 @@ static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
     if (rows512)
         e = launch_rows512<T>(a, m, H, false, st);
+    else if (rows1024)
+        e = launch_rows1024(true, a.spec, H, a.nx, a.ny, planes, a.twx, a.log2twx, (float)(-a.Ms), a.out_scale,
+                            a.L, st);
     else {
         k_rows_inverse<T><<<grid_rows, kRowThreads, smem_rows, st>>>((const C *)a.spec, H, a.nx, a.ny,
                                                                      a.log2Px, npair, (const C *)a.twx,

@@ -15,7 +15,9 @@
 //   k_columns_inverse  per (kx, group of planes): spec2 -> inverse transform
 //                      along y (decimation in time) -> spec[plane][kx][y < ny].
 //
-// The row transforms are those of the fused path (apply.cu).
+// For Py = 1024 the column transforms are those of cols1024.cu (two 512-point
+// radix-8 transforms per zero-padded column, same layouts).  The row transforms
+// are those of the fused path (apply.cu).
 #include "fft.cuh"
 #include "internal.h"
 #include "layout.cuh"
@@ -268,21 +270,31 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
                                   (int)smem_col)) != cudaSuccess)
         return e;
     dim3 gcol(Kx, (planes + G - 1) / G);
+    const bool c1024 = cols1024_supported(a.log2Py, a.ny, sizeof(T) == 8);
+    auto columns_inverse = [&]() -> cudaError_t {
+        if (c1024) return launch_cols1024(true, a.spec2, a.spec, a.ny, Kx, planes, a.twy, a.log2twy, st);
+        k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec, a.ny,
+                                                                    Kx, planes, G, a.log2Py,
+                                                                    (const C *)a.twy, a.log2twy);
+        return cudaGetLastError();
+    };
     cudaEvent_t *iev = a.inner_ev;
     if (iev && (e = cudaEventRecord(iev[0], st)) != cudaSuccess) return e;
-    k_columns_forward<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec, (C *)a.spec2, a.ny,
-                                                                Kx, planes, G, a.log2Py,
-                                                                (const C *)a.twy, a.log2twy);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (c1024) {
+        e = launch_cols1024(false, a.spec, a.spec2, a.ny, Kx, planes, a.twy, a.log2twy, st);
+    } else {
+        k_columns_forward<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec, (C *)a.spec2, a.ny,
+                                                                    Kx, planes, G, a.log2Py,
+                                                                    (const C *)a.twy, a.log2twy);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
     if (iev && (e = cudaEventRecord(iev[1], st)) != cudaSuccess) return e;
     if (a.contract_mode != 0) {
         e = a.contract_mode == 3 ? launch_contract_tc5(a, st) : launch_contract_gemm(a, a.contract_mode == 2, st);
         if (e != cudaSuccess) return e;
         if (iev && (e = cudaEventRecord(iev[2], st)) != cudaSuccess) return e;
-        k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec,
-                                                                    a.ny, Kx, planes, G, a.log2Py,
-                                                                    (const C *)a.twy, a.log2twy);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = columns_inverse()) != cudaSuccess) return e;
         if (iev && (e = cudaEventRecord(iev[3], st)) != cudaSuccess) return e;
         return cudaSuccess;
     }
@@ -298,10 +310,7 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
                                                        a.npairs, a.QyS, TU, a.full_pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (iev && (e = cudaEventRecord(iev[2], st)) != cudaSuccess) return e;
-    k_columns_inverse<T><<<gcol, kSplitThreads, smem_col, st>>>((const C *)a.spec2, (C *)a.spec, a.ny,
-                                                                Kx, planes, G, a.log2Py,
-                                                                (const C *)a.twy, a.log2twy);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = columns_inverse()) != cudaSuccess) return e;
     if (iev && (e = cudaEventRecord(iev[3], st)) != cudaSuccess) return e;
     return cudaSuccess;
 }

@@ -1,0 +1,118 @@
+// Two 512-point radix-8 transforms per zero-padded 1024-point sequence.
+//
+// A length-1024 sequence whose upper half is zero (a row or column of Eq.
+// FFT_v2 zero-padded from n <= 512) has the transform
+//   X[2k]     = DFT_512(x)[k]
+//   X[2k + 1] = DFT_512(x[n] W_1024^n)[k]                  (W_M = exp(-2 pi i / M))
+// and the inverse of a full spectrum Y, needed at n < 512 only (the crop), is
+//   y[n] = IDFT_512(Y_even)[n] + W_1024^-n IDFT_512(Y_odd)[n]
+// (no 1/N scaling).  Each 512-point transform is the register-resident radix-8
+// Stockham of fft8.cuh: 64 threads, three passes through shared memory.  One
+// group of 64 threads carries both transforms of one sequence (same positions,
+// same twiddles), so one thread holds X[2k] and X[2k + 1], or both halves of
+// y[n].  Used by the column (cols1024.cu) and row (rows1024.cu) kernels.
+#pragma once
+#include "fft8.cuh"
+
+namespace demag {
+namespace f1024 {
+
+
+constexpr int kF10Planes = 8;                 // sequences per block (plane columns or row pairs)
+constexpr int kF10Threads = 64 * kF10Planes;  // one 64-thread group per sequence
+// One padded 512-point column holds index p at p + p / 16 (544 slots); the
+// plane's second column starts 546 slots in (4 words mod 32) and planes are
+// 1092 slots apart (8 words mod 32), so that a warp of the transposed phase
+// (4 consecutive frequencies x 8 planes: a[k], b[k], a[k + 1], b[k + 1] of
+// each plane) needs the minimum two wavefronts.
+constexpr int kF10Col = 546;
+constexpr int kF10Plane = 2 * kF10Col;
+constexpr size_t kF10Smem = (size_t)kF10Planes * kF10Plane * sizeof(float2) + 512 * sizeof(float2);
+
+__device__ __forceinline__ int f10_pad(int p) { return p + (p >> 4); }
+
+__device__ __forceinline__ void f10_sync(int group) {
+    asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(64) : "memory");
+}
+
+// W_1024^m (m any integer) from the shared table of W_1024^k, k < 512.
+template <bool INV>
+__device__ __forceinline__ float2 f10_w(const float2 *tw, int m) {
+    m &= 1023;
+    float2 w = tw[m & 511];
+    if (m & 512) {
+        w.x = -w.x;
+        w.y = -w.y;
+    }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// Access pattern bases of a thread j (positions of the three Stockham passes
+// in the padded column; see fft8.cuh for the passes):
+//   positions j + 64 r        -> bj + 68 r
+//   pass-1 outputs 8 j + r    -> b1 + r
+//   pass-2 outputs            -> b2 + 8 r + r / 2
+struct F10Bases {
+    int bj, b1, b2;
+    __device__ explicit F10Bases(int j) : bj(j + (j >> 4)), b1(8 * j + (j >> 1)), b2(68 * (j >> 3) + (j & 7)) {}
+};
+
+// Passes 1..3 of both 512-point transforms of a plane; v[0] and v[1] hold the
+// pass-1 inputs (positions j + 64 r) on entry and the outputs (positions
+// j + 64 r) on return.  a, b: the plane's two padded columns.
+template <bool INV>
+__device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, float2 *b, const F10Bases &bs, int j,
+                                              int group, const float2 *tw) {
+    float2 *col[2] = {a, b};
+    // pass 1 (Ns = 1): no twiddles; outputs to 8 j + r
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        dft8<INV>(v[t]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) col[t][bs.b1 + r] = v[t][r];
+    }
+    f10_sync(group);
+    // pass 2 (Ns = 8): twiddles W_64^{r k}, k = j mod 8
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bj + 68 * r];
+    f10_sync(group);
+    {
+        const int k = j & 7;
+#pragma unroll
+        for (int r = 1; r < 8; ++r) {
+            const float2 w = f10_w<INV>(tw, 16 * r * k);  // W_64^{rk} = W_1024^{16 rk}
+            v[0][r] = c_mul(v[0][r], w);
+            v[1][r] = c_mul(v[1][r], w);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        dft8<INV>(v[t]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) col[t][bs.b2 + 8 * r + (r >> 1)] = v[t][r];
+    }
+    f10_sync(group);
+    // pass 3 (Ns = 64): twiddles W_512^{r j}; outputs to positions j + 64 r
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bj + 68 * r];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+        const float2 w = f10_w<INV>(tw, 2 * r * j);  // W_512^{rj} = W_1024^{2 rj}
+        v[0][r] = c_mul(v[0][r], w);
+        v[1][r] = c_mul(v[1][r], w);
+    }
+    dft8<INV>(v[0]);
+    dft8<INV>(v[1]);
+}
+
+__device__ __forceinline__ void f10_load_table(float2 *tws, const float2 *__restrict__ tw, int sh) {
+    for (int k = threadIdx.x; k < 512; k += blockDim.x) tws[k] = tw[k << sh];
+}
+
+}  // namespace f1024
+}  // namespace demag

@@ -107,6 +107,16 @@ unsigned take_wait_timeouts();
 cudaError_t launch_selftest_wait(long long limit, cudaStream_t st);
 
 // Dense-product contraction on the tcgen05 tensor cores (contract_tc5.cu).
+// Column transforms of the split path for Py = 1024 (two 512-point radix-8
+// transforms per column; cols1024.cu).
+bool cols1024_supported(int log2Py, int ny, bool fp64);
+cudaError_t launch_cols1024(bool inverse, const void *src, void *dst, int ny, int Kx, int planes, const void *tw,
+                            int log2tw, cudaStream_t st);
+// Row transforms for Px = 1024 (two 512-point radix-8 transforms per row pair;
+// rows1024.cu).
+bool rows1024_supported(int log2Px, int nx, bool fp64);
+cudaError_t launch_rows1024(bool inverse, const void *src, void *dst, int nx, int ny, int planes, const void *tw,
+                            int log2tw, float out_scale, const void *layer_scale, int L, cudaStream_t st);
 bool tc5_supported(int L, int B, int npairs);
 cudaError_t launch_contract_tc5(const ApplyArgs &a, cudaStream_t st);
 unsigned take_tc_timeouts();

@@ -45,6 +45,9 @@ def _fields(plan, m, Ms, paths):
     (32, 32, tuple(np.round(np.linspace(2.5, 0.6, 32), 3)), 16),
     (24, 20, tuple(np.round(np.linspace(0.7, 2.9, 10), 3)), 4),    # layers padded to 16, one row tile
     (17, 12, tuple(np.round(np.linspace(3.0, 0.5, 50), 3)), 6),    # layers padded to 56, two row tiles
+    (20, 300, (1.0, 0.5, 2.0, 0.8), 2),                            # Py = 1024 columns, ragged ny
+    (9, 512, (1.2, 0.7, 2.5), 3),                                  # Py = 1024 columns, ny = 512, odd L
+    (300, 11, (1.0, 0.5, 2.0, 0.8), 2),                            # Px = 1024 rows, ragged nx, odd ny
 ])
 def test_split_tf32_matches_oracle(nx, ny, th, B):
     m = inputs.random_unit_vectors((B, len(th), ny, nx), seed=len(th) + B)
@@ -85,12 +88,12 @@ def test_scale512_batch_sampled_against_oracle():
     assert rel_l2(H[6][state, target], ref) < 1e-5
 
 
-@pytest.mark.parametrize("path", [3, 4, 6])
-def test_split_tf32_adjoint_matches_oracle(path):
+@pytest.mark.parametrize("path,nx,ny", [(3, 13, 9), (4, 13, 9), (6, 13, 9), (6, 290, 270)])
+def test_split_tf32_adjoint_matches_oracle(path, nx, ny):
     """The adjoint (transposed-block convolution) through the dense-product
     contraction: sources scaled by 1/t_j and targets by t_i around the same
-    products."""
-    nx, ny, th, B = 13, 9, (1.0, 0.5, 2.0, 0.8), 3
+    products (290 x 270: the scales inside the 1024-point row kernels)."""
+    th, B = (1.0, 0.5, 2.0, 0.8), 3
     g = inputs.random_unit_vectors((B, len(th), ny, nx), seed=31)
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
     dm.demag_plan_set_path(plan.handle, path)

@@ -158,7 +158,9 @@ RAGGED = [(7, 5, (1.0, 0.5, 2.0)), (1, 1, (2.0,)), (33, 17, (0.9, 1.3, 0.4, 2.2)
           # 512-point transforms (radix-8 kernels), ragged rows and columns
           (200, 140, (1.0, 0.5, 2.0)), (129, 256, (0.8, 1.7)), (256, 131, (1.2,)),
           # 512-point columns under short rows, and 512-point rows over short columns
-          (5, 200, (1.0, 0.6)), (200, 6, (0.9, 2.0))]
+          (5, 200, (1.0, 0.6)), (200, 6, (0.9, 2.0)),
+          # 1024-point rows (two 512-point transforms per row pair), ragged and full
+          (300, 19, (1.0, 0.5, 2.0)), (512, 6, (1.3,))]
 
 
 @pytest.mark.parametrize("nx,ny,th", RAGGED)
