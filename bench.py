@@ -45,6 +45,8 @@ def parse_args():
                    help="run only the batched split-precision measurement and print its JSON")
     p.add_argument("--batched-n", type=int, default=512,
                    help="in-plane cells per side of the batched measurement (smaller for profiling)")
+    p.add_argument("--batched-layers", type=int, default=64,
+                   help="layers of the batched measurement (the first of its 64; fewer for profiling)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched (512x512x64, 16 states) and surrogate measurements")
     return p.parse_args()
@@ -214,7 +216,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_measurement(steps, peaks, n=512):
+def batched_measurement(steps, peaks, n=512, layers=64):
     """512 x 512 cells (n x n if given), 64 layers, 16 states per apply: the
     split-precision contraction on the tcgen05 tensor cores (path 6, the plan's
     default) and with warp-level MMAs (path 4), against the same products on
@@ -225,7 +227,7 @@ def batched_measurement(steps, peaks, n=512):
     import paper_1910_07054_gb300 as dm
     from paper_1910_07054_gb300 import inputs
     c = inputs.CONFIGS["scale512"]
-    th = [float(t) for t in inputs.thicknesses("scale512")]
+    th = [float(t) for t in inputs.thicknesses("scale512")][:layers]
     nx, ny, B, L = n, n, c["batch"], len(th)
     t0 = time.perf_counter()
     plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
@@ -233,8 +235,8 @@ def batched_measurement(steps, peaks, n=512):
     build_s = time.perf_counter() - t0
     m = torch.tensor(inputs.random_unit_vectors((B, L, ny, nx), seed=0), dtype=torch.float32, device="cuda")
     H = torch.empty_like(m)
-    out = {"workload": "%dx%d cells of 2x2 nm, 64 layers (t ~ U[0.5, 3] nm, seed 0), 16 random "
-                       "states per apply; inputs (%.2f GB)" % (nx, ny, B * L * 3 * nx * ny * 4 / 1e9),
+    out = {"workload": "%dx%d cells of 2x2 nm, %d layers (t ~ U[0.5, 3] nm, seed 0), 16 random "
+                       "states per apply; inputs (%.2f GB)" % (nx, ny, L, B * L * 3 * nx * ny * 4 / 1e9),
            "plan_create_s": build_s}
     fields = {}
     for path, name in ((4, "tensor_cores_3xtf32"), (6, "tcgen05_3xtf32"), (3, "fp32_cores")):
@@ -467,7 +469,8 @@ def main():
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
             with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
                 peaks = json.load(fh)
-        print(json.dumps(batched_measurement(max(args.steps, 1), peaks, args.batched_n)), flush=True)
+        print(json.dumps(batched_measurement(max(args.steps, 1), peaks, args.batched_n, args.batched_layers)),
+              flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

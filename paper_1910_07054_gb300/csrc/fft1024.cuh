@@ -27,7 +27,10 @@ constexpr int kF10Threads = 64 * kF10Planes;  // one 64-thread group per sequenc
 // each plane) needs the minimum two wavefronts.
 constexpr int kF10Col = 546;
 constexpr int kF10Plane = 2 * kF10Col;
-constexpr size_t kF10Smem = (size_t)kF10Planes * kF10Plane * sizeof(float2) + 512 * sizeof(float2);
+// Twiddle tables in shared memory: W_1024^k (k < 512), then W_64^m (m < 64),
+// then W_512^j (j < 64) for conflict-free pass-2 and pass-3 lookups.
+constexpr int kF10Tw = 512 + 64 + 64;
+constexpr size_t kF10Smem = (size_t)kF10Planes * kF10Plane * sizeof(float2) + kF10Tw * sizeof(float2);
 
 __device__ __forceinline__ int f10_pad(int p) { return p + (p >> 4); }
 
@@ -80,10 +83,13 @@ __device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, floa
         for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bj + 68 * r];
     f10_sync(group);
     {
+        // W_64^{rk} from the 64-entry table: for the 8 values of k in a warp the
+        // indices r k mod 64 fall in distinct banks (2-way at r = 4)
         const int k = j & 7;
 #pragma unroll
         for (int r = 1; r < 8; ++r) {
-            const float2 w = f10_w<INV>(tw, 16 * r * k);  // W_64^{rk} = W_1024^{16 rk}
+            float2 w = tw[512 + ((r * k) & 63)];
+            if (INV) w.y = -w.y;
             v[0][r] = c_mul(v[0][r], w);
             v[1][r] = c_mul(v[1][r], w);
         }
@@ -100,18 +106,40 @@ __device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, floa
     for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bj + 68 * r];
+    {
+        // W_512^{rj}: one lookup of W_512^j (consecutive j, no conflict), the
+        // other powers by products (within a few ulp of the table values)
+        float2 w[8];
+        w[1] = tw[576 + j];
+        if (INV) w[1].y = -w[1].y;
+        w[2] = c_mul(w[1], w[1]);
+        w[3] = c_mul(w[2], w[1]);
+        w[4] = c_mul(w[2], w[2]);
+        w[5] = c_mul(w[4], w[1]);
+        w[6] = c_mul(w[4], w[2]);
+        w[7] = c_mul(w[6], w[1]);
 #pragma unroll
-    for (int r = 1; r < 8; ++r) {
-        const float2 w = f10_w<INV>(tw, 2 * r * j);  // W_512^{rj} = W_1024^{2 rj}
-        v[0][r] = c_mul(v[0][r], w);
-        v[1][r] = c_mul(v[1][r], w);
+        for (int r = 1; r < 8; ++r) {
+            v[0][r] = c_mul(v[0][r], w[r]);
+            v[1][r] = c_mul(v[1][r], w[r]);
+        }
     }
     dft8<INV>(v[0]);
     dft8<INV>(v[1]);
 }
 
+// The three tables from the plan's table tw of W_{2^(10 + sh)}^k, k below half
+// its period (W_1024^(m + 512) = -W_1024^m).
 __device__ __forceinline__ void f10_load_table(float2 *tws, const float2 *__restrict__ tw, int sh) {
-    for (int k = threadIdx.x; k < 512; k += blockDim.x) tws[k] = tw[k << sh];
+    for (int k = threadIdx.x; k < kF10Tw; k += blockDim.x) {
+        const int m = k < 512 ? k : (k < 576 ? 16 * (k - 512) : 2 * (k - 576));  // exponent of W_1024, < 1024
+        float2 w = tw[(m & 511) << sh];
+        if (m & 512) {
+            w.x = -w.x;
+            w.y = -w.y;
+        }
+        tws[k] = w;
+    }
 }
 
 }  // namespace f1024
