@@ -143,21 +143,29 @@ def newton_surrogate(solver, net, t0, tol=1e-5, max_iter=20, layer=inputs.OPT_LA
                      bounds=(0.3, 6.0)):
     """Surrogate-proposed steps judged by the exact solver.
 
-    Each proposal is the root in t[layer] of the network's H_z shifted by the
-    residual of the last accepted exact evaluation (so the network supplies
-    the shape, the solver the level).  The solver evaluates it; the proposal
-    is accepted if |H_z| drops, otherwise an exact Newton step is taken.
+    Each proposal is the root in t[layer] of the network's H_z corrected to the
+    exact evaluations along the path: m(x) = hz_k + s (net(x) - net(t_k)), with
+    hz_k the last accepted exact value at t_k (the network supplies the shape,
+    the solver the level) and, once two exact points are known, s the ratio of
+    their exact to their network difference (the solver also fixes the scale;
+    s = 1 before that, clipped to [1/4, 4]).  The solver evaluates the proposal;
+    it is accepted if |H_z| drops, otherwise an exact Newton step with the
+    adjoint derivative is taken.
     Returns the history [(t_layer, hz, exact solves so far, 'accept' | 'exact')].
     """
     t = np.array(t0, dtype=np.float64)
     hz = solver.field(t)[2]
     hist = [(t[layer], hz, solver.solves, "start")]
+    prev = None  # (network value, exact value) at the previous exact point
     for _ in range(max_iter):
-        bias = hz - net.predict(t)[0, 2]
+        n_t = net.predict(t)[0, 2]
+        scale = 1.0
+        if prev is not None and abs(n_t - prev[0]) > 1e-12:
+            scale = float(np.clip((hz - prev[1]) / (n_t - prev[0]), 0.25, 4.0))
         tp = t.copy()
-        for _ in range(30):  # Newton on the surrogate alone: no exact solves
-            r = net.predict(tp)[0, 2] + bias
-            d = net.slope(tp, 2, layer)[0]
+        for _ in range(30):  # Newton on the corrected surrogate alone: no exact solves
+            r = scale * (net.predict(tp)[0, 2] - n_t) + hz
+            d = scale * net.slope(tp, 2, layer)[0]
             if d == 0.0:
                 break
             dt = -r / d
@@ -167,10 +175,12 @@ def newton_surrogate(solver, net, t0, tol=1e-5, max_iter=20, layer=inputs.OPT_LA
         step = tp[layer] - t[layer]
         hz_p = solver.field(tp)[2]
         if abs(hz_p) < abs(hz):
+            prev = (n_t, hz)
             t, hz = tp, hz_p
             hist.append((t[layer], hz, solver.solves, "accept"))
         else:
             hz0, d = solver.hz_and_slope(t, layer)
+            prev = (n_t, hz)
             t = t.copy()
             step = -hz0 / d
             t[layer] = float(np.clip(t[layer] + step, *bounds))
