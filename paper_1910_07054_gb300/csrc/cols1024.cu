@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_forward1024(const fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     float2 *tws = buf + kF10Planes * kF10Plane;
-    const int kx = blockIdx.x, g0 = blockIdx.y * kF10Planes;
+    const int kx = blockIdx.y, g0 = blockIdx.x * kF10Planes;
     const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
     const int g = g0 + group;
     f10_load_table(tws, tw, sh);
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_inverse1024(const fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     float2 *tws = buf + kF10Planes * kF10Plane;
-    const int kx = blockIdx.x, g0 = blockIdx.y * kF10Planes;
+    const int kx = blockIdx.y, g0 = blockIdx.x * kF10Planes;
     const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
     const int g = g0 + group;
     const int ng = min(kF10Planes, planes - g0);
@@ -120,7 +120,9 @@ cudaError_t launch_cols1024(bool inverse, const void *src, void *dst, int ny, in
     auto kern = inverse ? k_columns_inverse1024 : k_columns_forward1024;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF10Smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(Kx, (planes + kF10Planes - 1) / kF10Planes);
+    // plane groups fastest: the blocks that share the 128-byte lines of one
+    // spectrum2 row (8 planes each) run together and meet in L2
+    const dim3 grid((planes + kF10Planes - 1) / kF10Planes, Kx);
     kern<<<grid, kF10Threads, kF10Smem, st>>>((const float2 *)src, (float2 *)dst, ny, Kx, planes,
                                               (const float2 *)tw, log2tw - 10);
     return cudaGetLastError();
