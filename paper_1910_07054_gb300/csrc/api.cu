@@ -489,7 +489,7 @@ demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
     const bool fp64 = plan->precision == DEMAG_PREC_FP64;
     if (plan->umajor) {
-        if (path == 0) path = 4;
+        if (path == 0) path = tc5_supported(plan->L, plan->max_batch, plan->npairs) ? 6 : 4;
         if (path != 3 && path != 4 && path != 6)
             return fail(DEMAG_EUNSUPPORTED, "split-TF32 plans run path 3, 4 or 6");
         if (path == 6 && !tc5_supported(plan->L, plan->max_batch, plan->npairs))

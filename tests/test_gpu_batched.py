@@ -54,6 +54,9 @@ def test_split_tf32_matches_oracle(nx, ny, th, B):
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
     even = len(th) % 2 == 0
     assert plan.info["path"] == (6 if even else 4)  # tcgen05 (path 6) wherever it holds the plan
+    dm.demag_plan_set_path(plan.handle, 3)
+    dm.demag_plan_set_path(plan.handle, 0)  # back to the default
+    assert dm.demag_plan_info(plan.handle)["path"] == (6 if even else 4)
     paths = (4, 3, 6) if even else (4, 3)
     H = _fields(plan, m, 8e5, paths)
     plan.close()
