@@ -28,6 +28,8 @@ namespace demag {
 
 __constant__ double c_gl_x[kGLMax + 1][kGLMax];
 __constant__ double c_gl_w[kGLMax + 1][kGLMax];
+__constant__ float c_gl_xf[kGLMax + 1][kGLMax];  // the same rules rounded to float
+__constant__ float c_gl_wf[kGLMax + 1][kGLMax];
 
 // Gauss-Legendre nodes from the eigen-decomposition-free Newton iteration on
 // P_n, seeded with Tricomi's asymptotic node estimate.
@@ -70,6 +72,14 @@ demag_status upload_gauss_legendre() {
     for (int n = 1; n <= kGLMax; ++n) gauss_legendre_host(n, hx[n], hw[n]);
     DEMAG_CUDA(cudaMemcpyToSymbol(c_gl_x, hx, sizeof(hx)));
     DEMAG_CUDA(cudaMemcpyToSymbol(c_gl_w, hw, sizeof(hw)));
+    float fx[kGLMax + 1][kGLMax] = {}, fw[kGLMax + 1][kGLMax] = {};
+    for (int n = 0; n <= kGLMax; ++n)
+        for (int i = 0; i < kGLMax; ++i) {
+            fx[n][i] = (float)hx[n][i];
+            fw[n][i] = (float)hw[n][i];
+        }
+    DEMAG_CUDA(cudaMemcpyToSymbol(c_gl_xf, fx, sizeof(fx)));
+    DEMAG_CUDA(cudaMemcpyToSymbol(c_gl_wf, fw, sizeof(fw)));
     if (dev < 64) done[dev] = true;
     return DEMAG_OK;
 }
@@ -213,9 +223,12 @@ __device__ void closed_tensor(S X, S Y, S Z, const S t[3], const S s[3], S out[6
 // Difference density of one axis: u = xi - xi', xi on [0, a] (target),
 // xi' on [0, b] (source); T(u) = min(a, u + b) - max(0, u) on [-b, a], linear on
 // three pieces, each cut into `cuts` equal sub-pieces of n nodes.
+constexpr int kAxisMax = 48;  // double quadrature: node arrays up to this count per axis
+
 struct AxisRule {
     double a, b;
     double br[4];
+    double len[3];  // sub-piece length of each piece
     int cuts[3];
     int count;  // total nodes
 };
@@ -231,6 +244,7 @@ __device__ void axis_rule(AxisRule &r, double a, double b, double wcap, int n) {
     for (int p = 0; p < 3; ++p) {
         const double w = r.br[p + 1] - r.br[p];
         r.cuts[p] = w > 0.0 ? (int)ceil(w / wcap) : 0;
+        r.len[p] = r.cuts[p] > 0 ? w / r.cuts[p] : 0.0;
         r.count += r.cuts[p] * n;
     }
 }
@@ -244,7 +258,7 @@ __device__ __forceinline__ void axis_node(const AxisRule &r, int n, int k, doubl
         per = r.cuts[p] * n;
     }
     const int c = k / n, i = k - c * n;
-    const double len = (r.br[p + 1] - r.br[p]) / r.cuts[p];
+    const double len = r.len[p];
     const double lo = r.br[p] + len * c;
     const double half = 0.5 * len;
     u = lo + half + half * c_gl_x[n][i];
@@ -259,6 +273,46 @@ __device__ void quadrature_tensor(double X, double Y, double Z, const double t[3
     axis_rule(ry, t[1], s[1], wcap, n);
     axis_rule(rz, t[2], s[2], wcap, n);
     double hxx = 0, hyy = 0, hzz = 0, hxy = 0, hxz = 0, hyz = 0;
+    if (rx.count <= kAxisMax && ry.count <= kAxisMax && rz.count <= kAxisMax) {
+        // each axis's nodes once (the same values the loops below compute per use)
+        double xd[kAxisMax], xw[kAxisMax], yd[kAxisMax], yw[kAxisMax], zd[kAxisMax], zw[kAxisMax];
+        for (int k = 0; k < rx.count; ++k) {
+            double u;
+            axis_node(rx, n, k, u, xw[k]);
+            xd[k] = X + u;
+        }
+        for (int k = 0; k < ry.count; ++k) {
+            double u;
+            axis_node(ry, n, k, u, yw[k]);
+            yd[k] = Y + u;
+        }
+        for (int k = 0; k < rz.count; ++k) {
+            double u;
+            axis_node(rz, n, k, u, zw[k]);
+            zd[k] = Z + u;
+        }
+        for (int kx = 0; kx < rx.count; ++kx) {
+            const double dxv = xd[kx], wx = xw[kx];
+            for (int ky = 0; ky < ry.count; ++ky) {
+                const double dyv = yd[ky];
+                const double wxy = wx * yw[ky];
+                for (int kz = 0; kz < rz.count; ++kz) {
+                    const double dzv = zd[kz], wz = zw[kz];
+                    const double r2 = dxv * dxv + dyv * dyv + dzv * dzv;
+                    const double ir = 1.0 / sqrt(r2);
+                    const double ir2 = ir * ir;
+                    const double q = wxy * wz * ir * ir2 * ir2;  // weight / r^5
+                    const double q3 = 3.0 * q;
+                    hxx += q3 * dxv * dxv - q * r2;
+                    hyy += q3 * dyv * dyv - q * r2;
+                    hzz += q3 * dzv * dzv - q * r2;
+                    hxy += q3 * dxv * dyv;
+                    hxz += q3 * dxv * dzv;
+                    hyz += q3 * dyv * dzv;
+                }
+            }
+        }
+    } else
     for (int kx = 0; kx < rx.count; ++kx) {
         double ux, wx;
         axis_node(rx, n, kx, ux, wx);
@@ -301,41 +355,80 @@ __device__ __forceinline__ int far_nodes(double rho) {
     return rho >= 128.0 ? 3 : rho >= 32.0 ? 4 : rho >= 11.0 ? 5 : rho >= 5.5 ? 6 : rho >= 2.75 ? 7 : 8;
 }
 
-// Float plans: the far field carries no cancellation, so its quadrature runs
-// in float with nodes chosen for ~3e-8 of the largest component (below the
-// float rounding of the stored tensor).
-__device__ __forceinline__ int far_nodes_f32(double rho) {
-    return rho >= 64.0 ? 2 : rho >= 11.0 ? 3 : rho >= 4.0 ? 4 : rho >= 2.75 ? 5 : 6;
-}
-
 constexpr int kF32AxisMax = 64;
 
-// The quadrature of quadrature_tensor with the node sums in float.  Returns
-// false (nothing written) if an axis needs more than kF32AxisMax nodes.
-__device__ bool quadrature_tensor_f32(double X, double Y, double Z, const double t[3],
-                                      const double s[3], int n, double wcap, double out[6]) {
-    AxisRule rx, ry, rz;
-    axis_rule(rx, t[0], s[0], wcap, n);
-    axis_rule(ry, t[1], s[1], wcap, n);
-    axis_rule(rz, t[2], s[2], wcap, n);
-    if (rx.count > kF32AxisMax || ry.count > kF32AxisMax || rz.count > kF32AxisMax) return false;
-    float zd[kF32AxisMax], zw[kF32AxisMax];
-    for (int k = 0; k < rz.count; ++k) {
-        double u, w;
-        axis_node(rz, n, k, u, w);
-        zd[k] = (float)(Z + u);
-        zw[k] = (float)w;
+// The far-field quadrature of quadrature_tensor entirely in float (node
+// counts, sub-pieces, nodes and sums): for float plans, whose stored tensor
+// carries float rounding anyway, and because double arithmetic runs at a small
+// fraction of the float rate.  Node counts for ~3e-8 of the largest component.
+// Returns false (nothing written) if an axis needs more than kF32AxisMax nodes.
+struct AxisRuleF {
+    float a, b, br[4], len[3];
+    int cuts[3], count;
+};
+
+__device__ __forceinline__ void axis_rule_f(AxisRuleF &r, float a, float b, float inv_wcap, int n) {
+    r.a = a;
+    r.b = b;
+    r.br[0] = -b;
+    r.br[1] = fminf(0.f, a - b);
+    r.br[2] = fmaxf(0.f, a - b);
+    r.br[3] = a;
+    r.count = 0;
+    for (int p = 0; p < 3; ++p) {
+        const float w = r.br[p + 1] - r.br[p];
+        r.cuts[p] = w > 0.f ? (int)ceilf(w * inv_wcap) : 0;
+        r.len[p] = r.cuts[p] > 0 ? w / (float)r.cuts[p] : 0.f;
+        r.count += r.cuts[p] * n;
     }
+}
+
+// All nodes of one axis: positions off + u and weights (Gauss-Legendre on each
+// sub-piece times the difference density T(u)).
+__device__ __forceinline__ void axis_nodes_f(const AxisRuleF &r, int n, float off, float *d, float *w) {
+    int k = 0;
+    for (int p = 0; p < 3; ++p)
+        for (int c = 0; c < r.cuts[p]; ++c) {
+            const float half = 0.5f * r.len[p];
+            const float mid = r.br[p] + r.len[p] * (float)c + half;
+            for (int i = 0; i < n; ++i, ++k) {
+                const float u = mid + half * c_gl_xf[n][i];
+                const float T = fminf(r.a, u + r.b) - fmaxf(0.f, u);
+                d[k] = off + u;
+                w[k] = half * c_gl_wf[n][i] * T;
+            }
+        }
+}
+
+__device__ bool quadrature_tensor_f32(double Xd, double Yd, double Zd, const double t[3], const double s[3],
+                                      double gap, double out[6]) {
+    const float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
+    const float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
+    const float gapf = (float)gap, wcap = 0.5f * gapf, inv_wcap = 1.f / wcap;
+    float widest = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        const float br0 = -sf[k], br1 = fminf(0.f, tf[k] - sf[k]), br2 = fmaxf(0.f, tf[k] - sf[k]), br3 = tf[k];
+        const float ws[3] = {br1 - br0, br2 - br1, br3 - br2};
+        for (int p = 0; p < 3; ++p)
+            if (ws[p] > 0.f) widest = fmaxf(widest, ws[p] / ceilf(ws[p] * inv_wcap));
+    }
+    const float rho = gapf / widest;
+    const int n = rho >= 64.f ? 2 : rho >= 11.f ? 3 : rho >= 4.f ? 4 : rho >= 2.75f ? 5 : 6;
+    AxisRuleF rx, ry, rz;
+    axis_rule_f(rx, tf[0], sf[0], inv_wcap, n);
+    axis_rule_f(ry, tf[1], sf[1], inv_wcap, n);
+    axis_rule_f(rz, tf[2], sf[2], inv_wcap, n);
+    if (rx.count > kF32AxisMax || ry.count > kF32AxisMax || rz.count > kF32AxisMax) return false;
+    float xd[kF32AxisMax], xw[kF32AxisMax], yd[kF32AxisMax], yw[kF32AxisMax], zd[kF32AxisMax], zw[kF32AxisMax];
+    axis_nodes_f(rx, n, (float)Xd, xd, xw);
+    axis_nodes_f(ry, n, (float)Yd, yd, yw);
+    axis_nodes_f(rz, n, (float)Zd, zd, zw);
     float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
     for (int kx = 0; kx < rx.count; ++kx) {
-        double ux, wx;
-        axis_node(rx, n, kx, ux, wx);
-        const float dxv = (float)(X + ux);
+        const float dxv = xd[kx], wx = xw[kx];
         for (int ky = 0; ky < ry.count; ++ky) {
-            double uy, wy;
-            axis_node(ry, n, ky, uy, wy);
-            const float dyv = (float)(Y + uy);
-            const float wxy = (float)(wx * wy);
+            const float dyv = yd[ky];
+            const float wxy = wx * yw[ky];
             const float rxy = dxv * dxv + dyv * dyv;
             for (int kz = 0; kz < rz.count; ++kz) {
                 const float dzv = zd[kz];
@@ -381,6 +474,7 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
         closed_tensor<double>(X, Y, Z, t, s, out);
         return;
     }
+    if (far32 && quadrature_tensor_f32(X, Y, Z, t, s, gap, out)) return;
     const double wcap = 0.5 * gap;
     double widest = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -390,7 +484,6 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
         for (int p = 0; p < 3; ++p)
             if (ws[p] > 0.0) widest = fmax(widest, ws[p] / ceil(ws[p] / wcap));
     }
-    if (far32 && quadrature_tensor_f32(X, Y, Z, t, s, far_nodes_f32(gap / widest), wcap, out)) return;
     quadrature_tensor(X, Y, Z, t, s, far_nodes(gap / widest), wcap, out);
 }
 
