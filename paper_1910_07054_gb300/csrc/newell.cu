@@ -456,11 +456,10 @@ __device__ bool quadrature_tensor_f32(double Xd, double Yd, double Zd, const dou
     return true;
 }
 
-// The evaluation used everywhere: closed form while the gap between the two
-// cuboids is below the larger in-plane edge, quadrature (sub-pieces no wider
-// than half the gap) beyond.
-__device__ void tensor_eval(double X, double Y, double Z, const double t[3], const double s[3],
-                            double out[6], bool far32 = false) {
+// Distance between the two cuboids; true when it is below the larger in-plane
+// edge (the closed form applies there, the quadrature beyond).
+__device__ __forceinline__ bool near_pair(double X, double Y, double Z, const double t[3], const double s[3],
+                                          double &gap) {
     const double o[3] = {X, Y, Z};
     double gap2 = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -468,13 +467,23 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
         const double c = lo > 0.0 ? lo : (hi < 0.0 ? hi : 0.0);
         gap2 += c * c;
     }
-    const double gap = sqrt(gap2);
-    const double e = fmax(fmax(t[0], t[1]), fmax(s[0], s[1]));
-    if (gap < e) {
+    gap = sqrt(gap2);
+    return gap < fmax(fmax(t[0], t[1]), fmax(s[0], s[1]));
+}
+
+// The evaluation used everywhere: closed form while the gap between the two
+// cuboids is below the larger in-plane edge, quadrature (sub-pieces no wider
+// than half the gap) beyond.  With skip_near, near offsets are left to the
+// warp-parallel closed form of k_near_planes (returns false, nothing written).
+__device__ bool tensor_eval(double X, double Y, double Z, const double t[3], const double s[3],
+                            double out[6], bool far32 = false, bool skip_near = false) {
+    double gap;
+    if (near_pair(X, Y, Z, t, s, gap)) {
+        if (skip_near) return false;
         closed_tensor<double>(X, Y, Z, t, s, out);
-        return;
+        return true;
     }
-    if (far32 && quadrature_tensor_f32(X, Y, Z, t, s, gap, out)) return;
+    if (far32 && quadrature_tensor_f32(X, Y, Z, t, s, gap, out)) return true;
     const double wcap = 0.5 * gap;
     double widest = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -485,6 +494,7 @@ __device__ void tensor_eval(double X, double Y, double Z, const double t[3], con
             if (ws[p] > 0.0) widest = fmax(widest, ws[p] / ceil(ws[p] / wcap));
     }
     quadrature_tensor(X, Y, Z, t, s, far_nodes(gap / widest), wcap, out);
+    return true;
 }
 
 // ---- d/dt of the tensor ----------------------------------------------------
@@ -639,27 +649,10 @@ cudaError_t launch_tensor_points(int n, const double *geom, double *out, cudaStr
     return cudaGetLastError();
 }
 
-// One thread per (pair, q, p) with 0 <= p < nx, 0 <= q < ny: evaluate N(i <- j)
-// at (p dx, q dy, z_i - z_j) and write it, with the parity of each component
-// in X and Y (f even, g odd in x and y), at the up to four mirrored positions
-// of the circulant grid.
-__global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
-                                const int *__restrict__ pair_i, const int *__restrict__ pair_j,
-                                int nx, int ny, double dx, double dy, int log2Px, int log2Py,
-                                const double *__restrict__ z, const double *__restrict__ th,
-                                int far32) {
-    const long long total = (long long)np * nx * ny;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int p = (int)(idx % nx);
-    const int q = (int)((idx / nx) % ny);
-    const int P = (int)(idx / ((long long)nx * ny));
-    const int i = pair_i[p0 + P], j = pair_j[p0 + P];
-    const double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
-    double N[6];
-    tensor_eval(p * dx, q * dy, z[i] - z[j], t, s, N, far32 != 0);
-    const int Px = 1 << log2Px, Py = 1 << log2Py;
-    double2 *base = planes + (size_t)P * 3 * Px * Py;
+// Write N at offset (p, q) of a pair's three planes, with the parity of each
+// component in X and Y (f even, g odd in x and y), at the up to four mirrored
+// positions of the circulant grid.
+__device__ __forceinline__ void write_planes(double2 *base, int p, int q, int Px, int Py, const double N[6]) {
     for (int my = 0; my < 2; ++my) {
         if (my && q == 0) continue;
         const int yi = my ? Py - q : q;
@@ -674,6 +667,80 @@ __global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
             base[(size_t)2 * Px * Py + o] = make_double2(sgx * N[4], sgy * N[5]);
         }
     }
+}
+
+// The closed form at the near offsets, one warp per (pair, p <= pm, q <= qm):
+// the 6 x 64 signed Newell terms (closed_nxx / closed_nxy with their axis
+// permutations) are spread over the lanes, 12 each, and summed by a warp
+// reduction; offsets that are not near return (k_kernel_planes has them).
+__global__ void __launch_bounds__(32) k_near_planes(double2 *__restrict__ planes, int p0, int np,
+                                                    const int *__restrict__ pair_i,
+                                                    const int *__restrict__ pair_j, int nx, int ny, double dx,
+                                                    double dy, int log2Px, int log2Py,
+                                                    const double *__restrict__ z, const double *__restrict__ th,
+                                                    int pm) {
+    const int P = blockIdx.x, p = blockIdx.y % (pm + 1), q = blockIdx.y / (pm + 1);
+    if (p >= nx || q >= ny) return;
+    const int i = pair_i[p0 + P], j = pair_j[p0 + P];
+    const double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
+    const double o[3] = {p * dx, q * dy, z[i] - z[j]};
+    double gap;
+    if (!near_pair(o[0], o[1], o[2], t, s, gap)) return;
+    // component -> axis order of its arguments (xx yy zz: closed_nxx; xy xz yz: closed_nxy)
+    constexpr int kAx[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}, {0, 1, 2}, {0, 2, 1}, {2, 1, 0}};
+    const int lane = threadIdx.x;
+    double N[6];
+#pragma unroll 1
+    for (int c = 0; c < 6; ++c) {
+        const int A = kAx[c][0], Bx = kAx[c][1], C = kAx[c][2];
+        const double X = o[A], Y = o[Bx], Z = o[C];
+        const double TX = t[A], TY = t[Bx], TZ = t[C], SX = s[A], SY = s[Bx], SZ = s[C];
+        double acc = 0.0;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int tt = lane + 32 * h, a = tt >> 4, b = (tt >> 2) & 3, cc = tt & 3;
+            const double sgn = ((a == 0 || a == 3) ? 1.0 : -1.0) * ((b == 0 || b == 3) ? 1.0 : -1.0) *
+                               ((cc == 0 || cc == 3) ? 1.0 : -1.0);
+            const double sz = cc == 0 ? TZ : cc == 1 ? 0.0 : cc == 2 ? TZ - SZ : -SZ;
+            double v;
+            if (c < 3) {
+                const double sx = a == 0 ? 0.0 : a == 1 ? TX : a == 2 ? -SX : TX - SX;
+                const double sy = b == 0 ? TY : b == 1 ? 0.0 : b == 2 ? TY - SY : -SY;
+                v = newell_f<double>(X + sx, Y + sy, Z + sz);
+            } else {
+                const double sx = a == 0 ? TX : a == 1 ? 0.0 : a == 2 ? TX - SX : -SX;
+                const double sy = b == 0 ? 0.0 : b == 1 ? -SY : b == 2 ? TY : TY - SY;
+                v = newell_g<double>(X + sx, Y + sy, Z + sz);
+            }
+            acc += sgn * v;
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        N[c] = acc / (4.0 * kPi * (TX * TY * TZ));
+    }
+    if (lane == 0) {
+        const int Px = 1 << log2Px, Py = 1 << log2Py;
+        write_planes(planes + (size_t)P * 3 * Px * Py, p, q, Px, Py, N);
+    }
+}
+
+// One thread per (pair, q, p) with 0 <= p < nx, 0 <= q < ny: evaluate N(i <- j)
+// at (p dx, q dy, z_i - z_j) and write it (write_planes); near offsets are
+// k_near_planes'.
+__global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
+                                const int *__restrict__ pair_i, const int *__restrict__ pair_j,
+                                int nx, int ny, double dx, double dy, int log2Px, int log2Py,
+                                const double *__restrict__ z, const double *__restrict__ th,
+                                int far32) {
+    // blocks: pair fastest, then rows q (see plane_grid)
+    const int cpr = (nx + blockDim.x - 1) / blockDim.x;
+    const int P = blockIdx.x, q = blockIdx.y / cpr;
+    const int p = (blockIdx.y - q * cpr) * blockDim.x + threadIdx.x;
+    if (p >= nx) return;
+    const int i = pair_i[p0 + P], j = pair_j[p0 + P];
+    const double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
+    double N[6];
+    if (!tensor_eval(p * dx, q * dy, z[i] - z[j], t, s, N, far32 != 0, true)) return;
+    write_planes(planes + (size_t)P * 3 * ((size_t)1 << (log2Px + log2Py)), p, q, 1 << log2Px, 1 << log2Py, N);
 }
 
 // geom[n][12]: X, Y, Z, tx, ty, tz, sx, sy, sz, dtz, dsz, dZ -> out[n][6], dout[n][6]
@@ -705,12 +772,10 @@ cudaError_t launch_tensor_points_dt(int n, const double *geom, double *out, doub
 __global__ void k_dkernel_planes(double2 *__restrict__ planes, int p0, int np, int L, int layer,
                                  int nx, int ny, double dx, double dy, int log2Px, int log2Py,
                                  const double *__restrict__ z, const double *__restrict__ th) {
-    const long long total = (long long)np * nx * ny;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int p = (int)(idx % nx);
-    const int q = (int)((idx / nx) % ny);
-    const int P = (int)(idx / ((long long)nx * ny));
+    const int cpr = (nx + blockDim.x - 1) / blockDim.x;  // blocks as in k_kernel_planes
+    const int P = blockIdx.x, q = blockIdx.y / cpr;
+    const int p = (blockIdx.y - q * cpr) * blockDim.x + threadIdx.x;
+    if (p >= nx) return;
     const int i = (p0 + P) / L, j = (p0 + P) % L;
     const double dtz = i == layer ? 1.0 : 0.0, dsz = j == layer ? 1.0 : 0.0;
     const double dZ = (i > layer ? 1.0 : 0.0) - (j > layer ? 1.0 : 0.0);
@@ -736,12 +801,19 @@ __global__ void k_dkernel_planes(double2 *__restrict__ planes, int p0, int np, i
     }
 }
 
+// Grid of the plane kernels: x = pair, y = (row q, chunk of 128 offsets p).  The
+// pair index runs fastest, so the first blocks dispatched are the first rows of
+// every pair: the near-field offsets (closed form in double) and the dense
+// quadratures just beyond it, which take far longer than the rest, start first
+// and on different SMs instead of queueing behind one another.
+static dim3 plane_grid(int np, int nx, int ny, int bs) { return dim3(np, ny * ((nx + bs - 1) / bs)); }
+
 cudaError_t launch_dkernel_planes(double2 *planes, int p0, int np, int L, int layer, int nx, int ny,
                                   double dx, double dy, int log2Px, int log2Py, const double *z,
                                   const double *th, cudaStream_t st) {
-    const long long total = (long long)np * nx * ny;
-    k_dkernel_planes<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(planes, p0, np, L, layer, nx, ny, dx,
-                                                                      dy, log2Px, log2Py, z, th);
+    if (np <= 0) return cudaSuccess;
+    k_dkernel_planes<<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(planes, p0, np, L, layer, nx, ny, dx, dy,
+                                                                 log2Px, log2Py, z, th);
     return cudaGetLastError();
 }
 
@@ -749,10 +821,17 @@ cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pai
                                  const int *pair_j, int nx, int ny, double dx, double dy,
                                  int log2Px, int log2Py, const double *z, const double *th,
                                  cudaStream_t st, bool far32) {
-    const long long total = (long long)np * nx * ny;
-    const int bs = 128;
-    k_kernel_planes<<<(unsigned)((total + bs - 1) / bs), bs, 0, st>>>(
-        planes, p0, np, pair_i, pair_j, nx, ny, dx, dy, log2Px, log2Py, z, th, far32 ? 1 : 0);
+    if (np <= 0) return cudaSuccess;
+    // near offsets: gap >= (p - 1) dx along x (and likewise y), so only
+    // p <= ceil(e / dx), q <= ceil(e / dy) can be below e = max(dx, dy)
+    const double e = dx > dy ? dx : dy;
+    const int pm = (int)ceil(e / dx), qm = (int)ceil(e / dy);
+    k_near_planes<<<dim3(np, (pm + 1) * (qm + 1)), 32, 0, st>>>(planes, p0, np, pair_i, pair_j, nx, ny, dx, dy,
+                                                                log2Px, log2Py, z, th, pm);
+    cudaError_t e1 = cudaGetLastError();
+    if (e1 != cudaSuccess) return e1;
+    k_kernel_planes<<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(planes, p0, np, pair_i, pair_j, nx, ny, dx, dy,
+                                                                log2Px, log2Py, z, th, far32 ? 1 : 0);
     return cudaGetLastError();
 }
 
