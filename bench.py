@@ -47,6 +47,8 @@ def parse_args():
                    help="in-plane cells per side of the batched measurement (smaller for profiling)")
     p.add_argument("--batched-layers", type=int, default=64,
                    help="layers of the batched measurement (the first of its 64; fewer for profiling)")
+    p.add_argument("--grad-only", action="store_true",
+                   help="run only the differentiation measurement and print its JSON")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched (512x512x64, 16 states) and surrogate measurements")
     return p.parse_args()
@@ -272,6 +274,51 @@ def batched_measurement(steps, peaks, n=512, layers=64):
     return out
 
 
+def gradient_measurement(steps=20):
+    """The differentiation workload (256 x 256 cells of 2 nm, 10 layers with
+    t ~ U[0.7, 4] nm, seed 0, one random state): the adjoint apply A^T gH
+    (dH/dM) and d<H_z of layer 4>/d(thickness of layer 4), float plan.  The
+    first thickness gradient builds the double-precision derivative tensor
+    (all L^2 pairs); later ones reuse it (one apply of that tensor and a dot)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import inputs
+    c = inputs.CONFIGS["grad256"]
+    th = [float(t) for t in inputs.thicknesses("grad256")]
+    nx, ny, L, layer = c["nx"], c["ny"], len(th), 3
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_FP32)
+    info = plan.info
+    m = torch.tensor(inputs.random_unit_vectors((1, L, ny, nx), seed=0), dtype=torch.float32, device="cuda")
+    gH = torch.zeros_like(m)
+    gH[0, layer, 2] = 1.0 / (nx * ny)
+    gm = torch.empty_like(m)
+    for _ in range(3):
+        dm.demag_apply_adjoint(plan.handle, gH, inputs.MS_DEFAULT, gm, info=info)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        dm.demag_apply_adjoint(plan.handle, gH, inputs.MS_DEFAULT, gm, info=info)
+    e1.record()
+    torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1) / steps
+    t0 = time.perf_counter()
+    g = dm.demag_thickness_grad(plan.handle, m, gH, inputs.MS_DEFAULT, layer, info=info)
+    first_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g = dm.demag_thickness_grad(plan.handle, m, gH, inputs.MS_DEFAULT, layer, info=info)
+    again_ms = (time.perf_counter() - t0) / steps * 1e3
+    plan.close()
+    return {"workload": "256x256 cells of 2x2 nm, 10 layers (t ~ U[0.7, 4] nm, seed 0), 1 random state, "
+                        "float plan; d<H_z of layer 4>/dt_4 (1-based)",
+            "adjoint_apply_ms": adj_ms, "adjoint_evals_per_s": 1e3 / adj_ms,
+            "thickness_grad_first_s": first_s, "thickness_grad_cached_ms": again_ms,
+            "dhz_dt": float(g)}
+
+
 def surrogate_measurement():
     """Sec. 4-like optimisation on the 256 x 256 x 8 stack: 2000 solver samples
     (layer 5 in [0.5, 5] nm, the others +-10%), network training, and Newton on
@@ -408,6 +455,7 @@ def run_ours(args):
             except ValueError:
                 peaks = {}
         extras["batched"] = batched_measurement(3, peaks)
+        extras["gradient"] = gradient_measurement()
         extras["surrogate"] = surrogate_measurement()
 
     line = None
@@ -471,6 +519,9 @@ def main():
                 peaks = json.load(fh)
         print(json.dumps(batched_measurement(max(args.steps, 1), peaks, args.batched_n, args.batched_layers)),
               flush=True)
+        return
+    if args.grad_only:
+        print(json.dumps(gradient_measurement()), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

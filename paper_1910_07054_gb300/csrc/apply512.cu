@@ -301,6 +301,8 @@ struct Ring8 {
     static constexpr int kFit = (kRingBudget - kCols * kColR * 8) / (kStage8 * 4);
     static constexpr int kStages = kPairs < kFit ? kPairs : kFit;  // pair slots of the ring
     static constexpr size_t kSmem = (size_t)kCols * kColR * 8 + (size_t)kStages * kStage8 * 4;
+    // a row's pairs must all be resident at once (the row waits for all of them)
+    static_assert(kStages >= L, "the ring must hold the longest pair row");
     // first stored pair of row i (pairs (i, j >= i), row by row)
     static __host__ __device__ constexpr int first(int i) { return i * L - (i * (i - 1)) / 2; }
 };
@@ -808,7 +810,7 @@ static cudaError_t launch_ring8(const ApplyArgs &a, cudaStream_t st) {
 // The streamed kernel takes float plans with L <= 8, the pair-symmetric
 // tensor with 260 stored frequencies per row and a 16-byte aligned tensor.
 static bool ring8_supported(const ApplyArgs &a, bool fp64) {
-    if (fp64 || a.full_pairs || a.L < 1 || a.L > 8 || a.QyS != kQyS8 || a.log2Py != 9) return false;
+    if (fp64 || a.full_pairs || a.L < 1 || a.L > 11 || a.QyS != kQyS8 || a.log2Py != 9) return false;
     return (reinterpret_cast<uintptr_t>(a.tensor) & 15) == 0;
 }
 
@@ -821,7 +823,10 @@ static cudaError_t launch_ring8_any(const ApplyArgs &a, cudaStream_t st) {
     case 5: return launch_ring8<5>(a, st);
     case 6: return launch_ring8<6>(a, st);
     case 7: return launch_ring8<7>(a, st);
-    default: return launch_ring8<8>(a, st);
+    case 8: return launch_ring8<8>(a, st);
+    case 9: return launch_ring8<9>(a, st);
+    case 10: return launch_ring8<10>(a, st);
+    default: return launch_ring8<11>(a, st);
     }
 }
 

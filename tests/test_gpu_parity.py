@@ -173,9 +173,9 @@ def test_ragged_grids_match_oracle_hybrid(nx, ny, th, prec):
     assert rel_l2(H, H_ref) < (TOL64 if prec == dm.PREC_FP64 else TOL32)
 
 
-@pytest.mark.parametrize("L", range(1, 9))
+@pytest.mark.parametrize("L", range(1, 12))
 def test_streamed_columns_every_layer_count(L):
-    """Float plans with 512-point columns and L <= 8 take the kernel that streams
+    """Float plans with 512-point columns and L <= 11 take the kernel that streams
     the tensor through shared memory (every unrolled pair count, ragged grid,
     batch of two states); no bounded wait may give up."""
     rng = np.random.default_rng(40 + L)
