@@ -499,6 +499,7 @@ def run_ours(args):
             "clocks": clk,
             "plan_create_s": plan_s,
             "batched": extras.get("batched"),
+            "gradient": extras.get("gradient"),
             "surrogate": extras.get("surrogate"),
             "wall_s_timed_loop": wall,
         }
