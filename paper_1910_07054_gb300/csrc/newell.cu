@@ -853,10 +853,9 @@ __global__ void k_fft_rows_f64(double2 *__restrict__ data, long long nrows, int 
 
 // Column FFTs of planes [nplanes][Py][Px]: a block takes `tile` adjacent columns.
 __global__ void k_fft_cols_f64(double2 *__restrict__ data, int log2Px, int log2Py, int tile,
-                               const double2 *__restrict__ tw, int log2tw) {
+                               int tiles_per_plane, const double2 *__restrict__ tw, int log2tw) {
     extern __shared__ double2 sm_cols[];
     const int Px = 1 << log2Px, Py = 1 << log2Py;
-    const int tiles_per_plane = Px / tile;
     const int plane = blockIdx.x / tiles_per_plane;
     const int x0 = (blockIdx.x % tiles_per_plane) * tile;
     double2 *base = data + (size_t)plane * Px * Py + x0;
@@ -897,8 +896,12 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
     smem = (size_t)tile * (Py + 1) * sizeof(double2);
     e = cudaFuncSetAttribute(k_fft_cols_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_cols_f64<<<(unsigned)((long long)nplanes * (Px / tile)), 256, smem, st>>>(
-        planes, log2Px, log2Py, tile, twy, log2twy);
+    // only the columns kx <= Px/2 that k_extract reads: each packed plane holds two
+    // components whose spectra are both real or both imaginary (their parities
+    // in x and y), so no Hermitian partner at Px - kx is needed
+    const int ntile = (Px / 2 + 1 + tile - 1) / tile;  // tile <= Px/2 or tile = Px: inside the plane
+    k_fft_cols_f64<<<(unsigned)((long long)nplanes * ntile), 256, smem, st>>>(planes, log2Px, log2Py, tile,
+                                                                              ntile, twy, log2twy);
     return cudaGetLastError();
 }
 
