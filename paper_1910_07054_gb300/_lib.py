@@ -167,7 +167,9 @@ def demag_apply(plan, m, Ms, H, stream=None, info=None):
 
 
 def demag_plan_set_path(plan, path):
-    """1: fused column kernel, 2: split column kernels, 0: the plan's default."""
+    """0: the plan's default; 1: fused column kernel, 2: split column kernels;
+    split-precision plans: 3 (FP32 cores), 4 (warp-level TF32 MMAs), 6 (tcgen05,
+    their default where it holds the plan).  See demag_plan_set_path in demag.h."""
     _check(lib().demag_plan_set_path(ctypes.c_void_p(plan), int(path)), "demag_plan_set_path")
 
 
