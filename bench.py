@@ -72,6 +72,29 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank):
+    """Seed of a rank's magnetization states: every rank evaluates its own
+    independent states (the path shards over states, no data-path collective)."""
+    return rank
+
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The slowest rank's value (all ranks receive it); the value itself on one
+    process.  NCCL ranks pass device="cuda", gloo ranks the CPU."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, batch_per_rank, step_ms):
+    """Evaluations per second of the whole job: every rank's states in the time
+    of the slowest rank's step."""
+    return world * batch_per_rank / (step_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the GPU works."""
 
@@ -370,7 +393,7 @@ def run_ours(args):
     c, th, desc = workload()
     nx, ny, L, B = c["nx"], c["ny"], len(th), c["batch"]
     Ms = inputs.MS_DEFAULT
-    m_np = inputs.mram_magnetization(nx, ny, L, seed=rank, batch=B)
+    m_np = inputs.mram_magnetization(nx, ny, L, seed=rank_seed(rank), batch=B)
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
@@ -404,12 +427,8 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    T = float(step_ms.mean())
-    if dist:
-        t = torch.tensor([T], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T = float(t.item())
-    value = world * B / (T * 1e-3)
+    T = max_over_ranks(float(step_ms.mean()), dist, "cuda")
+    value = whole_job_value(world, B, T)
 
     # per-kernel device times (same kernels, events between them, cold L2 each step)
     nk = min(args.steps, 200)
@@ -427,7 +446,7 @@ def run_ours(args):
     e0 = time.perf_counter()
     for _ in range(ne):
         dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
-    e2e_s = (time.perf_counter() - e0) / ne
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
     clk = clocks.stop()
 
     # algorithmic bytes per launch (float32, B states)
@@ -493,7 +512,7 @@ def run_ours(args):
                          "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes": stage_bytes[dom]},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * B / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": field,
+            "e2e": {"value": whole_job_value(world, B, e2e_s * 1e3), "unit": "evals/s", "h2d_bytes_per_step": field,
                     "d2h_bytes_per_step": field},
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
