@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
         }
         // m of layers >= KR stays in registers (m_j serves rows 0..j, so the
         // upper layers are reused most); lower layers are read when used
-        constexpr int KR = L <= 8 ? L / 2 : L - 2;
+        constexpr int KR = L / 2;
         C acc[L][3], m[L][3];
 #pragma unroll
         for (int l = 0; l < L; ++l)
