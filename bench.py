@@ -164,11 +164,52 @@ def measured_hbm_peak():
     return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash():
+def code_only(text):
+    """C/C++ source with its comments (// to end of line, /* ... */) and every
+    run of whitespace outside literals reduced to one space, string and
+    character literals kept: what the compiled kernels depend on."""
+    out, i, n = [], 0, len(text)
+
+    def space():
+        if out and out[-1] != " ":
+            out.append(" ")
+
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+            space()
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            space()
+        elif c.isspace():
+            i += 1
+            space()
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def kernel_source_hash(read=None):
+    """Hash of the headline kernels' sources, comments excluded (a comment edit
+    does not change the counters recorded for them)."""
     h = hashlib.sha256()
     for name in ("apply.cu", "apply512.cu", "fft.cuh", "fft8.cuh"):
-        with open(os.path.join(ROOT, "paper_1910_07054_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_1910_07054_gb300", "csrc", name), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(name)
+        h.update(code_only(text).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256, 2) k_columns_fused8(typename cpx_of<T>::t
 }
 
 // ---------------------------------------------------------------------------
-// Float columns for L <= 8 layers: the tensor streamed through shared memory.
+// Float columns for L <= 11 layers: the tensor streamed through shared memory.
 //
 // One block of 512 threads per (kx, state).  The 3L columns are transformed by
 // eight 64-thread groups; in the contraction thread p owns the y-frequency
@@ -807,8 +807,9 @@ static cudaError_t launch_ring8(const ApplyArgs &a, cudaStream_t st) {
                       (const float *)a.tensor, (const float *)a.ratio, Kx, a.ny, (const float2 *)a.twy);
 }
 
-// The streamed kernel takes float plans with L <= 8, the pair-symmetric
-// tensor with 260 stored frequencies per row and a 16-byte aligned tensor.
+// The streamed kernel takes float plans with L <= 11 (its ring holds a full
+// pair row), the pair-symmetric tensor with 260 stored frequencies per row and
+// a 16-byte aligned tensor.
 static bool ring8_supported(const ApplyArgs &a, bool fp64) {
     if (fp64 || a.full_pairs || a.L < 1 || a.L > 11 || a.QyS != kQyS8 || a.log2Py != 9) return false;
     return (reinterpret_cast<uintptr_t>(a.tensor) & 15) == 0;

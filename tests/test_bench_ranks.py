@@ -83,3 +83,15 @@ def test_single_process_helpers():
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.whole_job_value(1, 16, 2.0) == 8000.0
     assert bench.rank_seed(0) != bench.rank_seed(1)
+
+
+def test_kernel_hash_ignores_comments_and_layout_only():
+    sys.path.insert(0, ROOT)
+    import bench
+    a = 'int f(int x) {  // add one\n  return x + 1; /* done */ }\nconst char *s = "a // b";\n'
+    b = 'int f(int x) {\n    return x + 1;\n}\n// a note\nconst char *s = "a // b";\n'
+    c = 'int f(int x) { return x + 2; }\nconst char *s = "a // b";\n'
+    d = 'int f(int x) { return x + 1; }\nconst char *s = "a //  b";\n'
+    assert bench.code_only(a) == bench.code_only(b)      # comments and whitespace only
+    assert bench.code_only(a) != bench.code_only(c)      # code
+    assert bench.code_only(a) != bench.code_only(d)      # inside a literal
