@@ -1,11 +1,18 @@
 #!/usr/bin/env python3
 """Benchmark of the hybrid demagnetization field (Eq. FFT_v2) on GB300.
 
-One step = one demagnetization-field evaluation of the workload (forward row
-FFTs, fused column FFT + layer contraction + inverse column FFT, inverse row
-FFTs) through the C ABI on device-resident inputs.  A 256 MB buffer (twice the
-L2) is written between timed steps so that every step starts from a cold L2;
-steps are timed with CUDA events on the launching stream.
+One step = one application of the method to a batch of magnetization states
+through the C ABI on device-resident inputs.  The headline workload is the
+largest single-GPU stack: 512 x 512 cells of 2 x 2 nm, 64 layers with
+thicknesses uniform in [0.5, 3] nm (seed 0), 16 random states per apply, float
+FFTs and the split-precision contraction (three TF32 passes, float
+accumulation) on the tcgen05 tensor cores.  Its inputs (3.2 GB of m, a 13.1 GB
+tensor) are far larger than the 129 MB L2, so consecutive steps start cold.
+Steps are timed with CUDA events on the launching stream.
+
+Beside it: the 256 x 256 x 8 MRAM-like stack as a full block of its own (a
+256 MB buffer written between its steps), the split-precision variants, the
+differentiation and the surrogate workloads, and the oracle on the host cores.
 
 Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
 independently seeded states on its own GPU (replicas, weak scaling) and the
@@ -26,6 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "demag evals/s and Gcell-layers/s at ≤1e-5 rel L2 vs FP64 oracle; % HBM peak"
+HEADLINE = "scale512"
 WORKLOAD = "mram256"
 FLUSH_BYTES = 256 << 20
 HBM_FALLBACK_GBS = 6800.0
@@ -34,11 +42,12 @@ HBM_FALLBACK_GBS = 6800.0
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
-    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--cpu-budget", type=float, default=20.0,
-                   help="seconds of oracle evaluation for the CPU baseline sample")
+                   help="seconds of oracle evaluation for the 256x256x8 CPU baseline sample")
+    p.add_argument("--no-allcore", action="store_true", help="skip the all-core oracle timing")
     p.add_argument("--no-parity", action="store_true", help="skip the oracle field comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--batched-only", action="store_true",
@@ -50,7 +59,10 @@ def parse_args():
     p.add_argument("--grad-only", action="store_true",
                    help="run only the differentiation measurement and print its JSON")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the batched (512x512x64, 16 states) and surrogate measurements")
+                   help="skip the 256x256x8 block, the split-precision variants, the differentiation and "
+                        "the surrogate measurements")
+    p.add_argument("--mram-only", action="store_true",
+                   help="run only the 256x256x8 block (device timing) and print its JSON")
     return p.parse_args()
 
 
@@ -199,11 +211,11 @@ def code_only(text):
     return "".join(out)
 
 
-def kernel_source_hash(read=None):
-    """Hash of the headline kernels' sources, comments excluded (a comment edit
-    does not change the counters recorded for them)."""
+def kernel_source_hash(names=("apply.cu", "apply512.cu", "fft.cuh", "fft8.cuh"), read=None):
+    """Hash of kernel sources, comments excluded (a comment edit does not change
+    the counters recorded for them)."""
     h = hashlib.sha256()
-    for name in ("apply.cu", "apply512.cu", "fft.cuh", "fft8.cuh"):
+    for name in names:
         if read is None:
             with open(os.path.join(ROOT, "paper_1910_07054_gb300", "csrc", name), encoding="utf-8") as fh:
                 text = fh.read()
@@ -215,21 +227,31 @@ def kernel_source_hash(read=None):
 
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current source of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
-        return None
     ent = rec.get("kernels", {}).get(kernel)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    if ent is None or ent.get("source_hash") != kernel_source_hash(tuple(ent.get("sources", ()))):
+        return None
+    return ent.get("dram_bytes_per_launch")
 
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---- oracle (host cores) --------------------------------------------------------
 
 def oracle_setup(c, th):
-    """Oracle spectra of the workload's layer kernels (float64, CPU)."""
+    """Oracle spectra of the 256 x 256 x 8 workload's layer kernels (float64, CPU)."""
     from oracle import demag as odm
     from oracle import newell as onw
     Kq = onw.layer_kernels(c["nx"], c["ny"], c["dx"], c["dy"], th, mode=onw.READING_D, full=False)
@@ -250,43 +272,269 @@ def oracle_timed(Khat, m_np, Ms, budget_s, max_evals):
     return times, H
 
 
+def headline_workload():
+    from paper_1910_07054_gb300 import inputs
+    c = inputs.CONFIGS[HEADLINE]
+    th = [float(t) for t in inputs.thicknesses(HEADLINE)]
+    desc = ("layer scaling + batch: %dx%d cells of %gx%g nm, %d layers with thicknesses uniform in [%g, %g] nm "
+            "(seed %d), %d random unit-vector states per apply (normalised N(0,1) triples); Ms = %g A/m; float32 "
+            "FFTs, split-precision contraction (3xTF32, float accumulate) on the tcgen05 tensor cores, float64 "
+            "tensor set-up"
+            % (c["nx"], c["ny"], c["dx"], c["dy"], len(th), c["thickness_range"][0], c["thickness_range"][1],
+               c["seed"], c["batch"], inputs.MS_DEFAULT))
+    return c, th, desc
+
+
+def headline_config(c, th, desc, world, info=None):
+    cfg = {"workload": desc, "nx": c["nx"], "ny": c["ny"], "layers": len(th), "batch_per_gpu": c["batch"],
+           "padded_fft": [info["Px"], info["Py"]] if info else [2 * c["nx"], 2 * c["ny"]],
+           "l2": "inputs larger than L2 (m 3.2 GB, tensor 13.1 GB per step against a 129 MB L2); no flush",
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    return cfg
+
+
+# The sampled oracle evaluation of the headline workload: one target layer of
+# one state, Eq. FFT_v2 pair by pair (oracle.demag.hybrid_targets as it
+# stands: forward FFTs of the state's 3L source planes, per source layer the
+# spectra of the pair kernel and the 3x3 products, inverse FFT of the target's
+# three planes).  The pair kernels of that target row are evaluated once
+# beforehand (tensor set-up, not timed).  A whole state is L such target
+# layers, so evals/s = 1 / (L * sample time); this overstates the oracle's cost
+# slightly (the source FFTs would be shared between targets) and is stated so.
+SAMPLE_TARGET = 37
+
+
+def headline_pair_kernels(c, th, target=SAMPLE_TARGET):
+    import numpy as np
+    from oracle import newell as onw
+    return np.stack([onw.pair_kernel(c["nx"], c["ny"], c["dx"], c["dy"], th, target, j)
+                     for j in range(len(th))])
+
+
+def headline_oracle_sample(pk, m_state, Ms, target=SAMPLE_TARGET):
+    from oracle import demag as odm
+    t0 = time.perf_counter()
+    H = odm.hybrid_targets(lambda i, j: pk[j], m_state, Ms, [target])[target]
+    return time.perf_counter() - t0, H
+
+
+def _allcore_worker(job):
+    """One process of the all-core oracle timing (spawned): the headline sample
+    on its own state, started at a common wall-clock instant."""
+    import numpy as np
+    from oracle import demag as odm
+    pk_path, m_path, state, Ms, target, start_at = job
+    pk = np.load(pk_path, mmap_mode="r")
+    m = np.array(np.load(m_path, mmap_mode="r")[state])
+    while time.time() < start_at:
+        time.sleep(0.005)
+    t0 = time.time()
+    odm.hybrid_targets(lambda i, j: np.asarray(pk[j]), m, Ms, [target])
+    return t0, time.time()
+
+
+def headline_oracle_allcore(pk, m_np, Ms, L):
+    """The headline sample run concurrently by one spawned process per core (as
+    many as the host's free memory allows, about 6 GB each): evals/s of the
+    whole host."""
+    import multiprocessing as mp
+    import shutil
+
+    import numpy as np
+    ncpu = os.cpu_count() or 1
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 0
+    nproc = max(1, min(ncpu, int(avail // (6 << 30))))
+    base = "/dev/shm" if os.path.isdir("/dev/shm") else None
+    tmp = tempfile.mkdtemp(prefix="demag_oracle_", dir=base)
+    try:
+        pk_path, m_path = os.path.join(tmp, "pk.npy"), os.path.join(tmp, "m.npy")
+        np.save(pk_path, pk)
+        np.save(m_path, m_np[:min(nproc, m_np.shape[0])])
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(nproc) as pool:
+            pool.map(abs, range(nproc))  # workers started and imported before the clock
+            start = time.time() + 2.0
+            jobs = [(pk_path, m_path, k % min(nproc, m_np.shape[0]), Ms, SAMPLE_TARGET, start)
+                    for k in range(nproc)]
+            spans = pool.map(_allcore_worker, jobs)
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    wall = max(t1 for _, t1 in spans) - min(t0 for t0, _ in spans)
+    return {"value": nproc / (L * wall), "unit": "evals/s", "cores": nproc, "kind": "oracle",
+            "host_cpus": ncpu,
+            "sample": "%d concurrent spawned processes, each one target layer of one state (the single-thread "
+                      "sample), %.1f s wall; evals/s = processes / (%d layers x wall)" % (nproc, wall, L)}
+
+
 def run_reference(args):
-    """The oracle (float64 numpy + C) on the host cores, whole evaluations of the
-    same workload; at most --steps evaluations after --warmup, bounded in time."""
+    """The oracle (float64 numpy + C) on the host cores for the headline
+    workload, sampled: each step is one target layer of one state (see
+    headline_oracle_sample), at most --steps samples after at most one warm-up
+    sample, bounded to about a minute."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import numpy as np
     from paper_1910_07054_gb300 import inputs
-    c, th, desc = workload()
-    m = inputs.mram_magnetization(c["nx"], c["ny"], len(th), seed=0, batch=c["batch"])
+    c, th, desc = headline_workload()
+    L = len(th)
+    m = inputs.random_unit_vectors((1, L, c["ny"], c["nx"]), seed=0)
     t0 = time.perf_counter()
-    Khat = oracle_setup(c, th)
+    pk = headline_pair_kernels(c, th)
     setup_s = time.perf_counter() - t0
     warm = min(args.warmup, 1)
-    oracle_timed(Khat, m, inputs.MS_DEFAULT, 0.0, warm)
-    times, _ = oracle_timed(Khat, m, inputs.MS_DEFAULT, args.cpu_budget * 3, args.steps)
+    for _ in range(warm):
+        headline_oracle_sample(pk, m[0], inputs.MS_DEFAULT)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max(args.steps, 1):
+        times.append(headline_oracle_sample(pk, m[0], inputs.MS_DEFAULT)[0])
+        if time.perf_counter() - t_start > 60.0:
+            break
     per = float(np.mean(times))
-    value = c["batch"] / per
-    sample = ("%d whole evaluations of the workload (of %d steps requested) after %d warm-up, oracle "
-              "float64 hybrid (numpy FFT, single thread); tensor set-up %.1f s not timed"
+    value = 1.0 / (L * per)
+    sample = ("%d samples (of %d steps requested) after %d warm-up, each one target layer of one state: oracle "
+              "float64 hybrid_targets (numpy FFT, single thread) over the 64 source layers; evals/s = 1 / (64 x "
+              "sample time); pair kernels of the target row evaluated beforehand in %.1f s, not timed"
               % (len(times), args.steps, warm, setup_s))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 0,
             "steps": len(times), "warmup": warm, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "parallelism": "host cores"},
-            "gcell_layers_per_s": c["nx"] * c["ny"] * len(th) * value / 1e9,
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": dict(headline_config(c, th, desc, 1), parallelism="host cores"),
+            "gcell_layers_per_s": c["nx"] * c["ny"] * L * value / 1e9,
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def batched_measurement(steps, peaks, n=512, layers=64):
+# ---- GPU measurements ---------------------------------------------------------------
+
+def split_stage_names(info):
+    r = "1024" if info["Px"] == 1024 else ""
+    cfwd = "k_columns_forward1024" if info["Py"] == 1024 else "k_columns_forward"
+    cinv = "k_columns_inverse1024" if info["Py"] == 1024 else "k_columns_inverse"
+    contract = {6: "k_contract_tc5", 4: "k_contract_tc", 3: "k_contract_gemm"}.get(info["path"], "k_contract")
+    return ["k_rows_forward" + r, cfwd, contract, cinv, "k_rows_inverse" + r]
+
+
+def split_stage_bytes(info, B):
+    """Algorithmic bytes of the five split-path kernels (float32): field, row
+    spectrum [B][L][3][Kx][ny], column spectrum [Kx][Py][B][L][3] and the
+    compact tensor (6 reals per stored pair and entry, Kx x (Py/2+1) entries)."""
+    L, nx, ny = info["L"], info["nx"], info["ny"]
+    Kx, Py, Qy = info["Px"] // 2 + 1, info["Py"], info["Py"] // 2 + 1
+    field = B * L * 3 * ny * nx * 4
+    spec = B * L * 3 * Kx * ny * 8
+    spec2 = B * L * 3 * Kx * Py * 8
+    tensor = Kx * Qy * info["npairs"] * 6 * 4
+    return [field + spec, spec + spec2, 2 * spec2 + tensor, spec2 + spec, spec + field], field, tensor
+
+
+def time_steps(run, steps, stream, before=None):
+    """CUDA-event time of each of `steps` calls of run(), on `stream`."""
+    import numpy as np
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        if before is not None:
+            before(k)
+        starts[k].record(stream)
+        run()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+
+
+def mram_block(args, world, rank, dist, peaks, with_oracle):
+    """The 256 x 256 x 8 MRAM-like stack (float32, one state per apply): device
+    timing with a 256 MB L2 flush between steps, per-kernel times and the
+    roofline of the dominant kernel, end to end through pinned host buffers,
+    parity and the single-thread oracle."""
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import inputs
+    c, th, desc = workload()
+    nx, ny, L, B = c["nx"], c["ny"], len(th), c["batch"]
+    Ms = inputs.MS_DEFAULT
+    m_np = inputs.mram_magnetization(nx, ny, L, seed=rank_seed(rank), batch=B)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_FP32, max_batch=B)
+    plan_s = time.perf_counter() - t0
+    info = plan.info
+    m = torch.tensor(m_np, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(m)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    steps = max(args.steps, 20)
+    for k in range(max(args.warmup, 3)):
+        flush.fill_(float(k))
+        dm.demag_apply(plan.handle, m, Ms, H, stream, info)
+    torch.cuda.synchronize()
+    step_ms = time_steps(lambda: dm.demag_apply(plan.handle, m, Ms, H, stream, info), steps, stream,
+                         before=lambda k: flush.fill_(float(k)))
+    T = max_over_ranks(float(step_ms.mean()), dist, "cuda")
+    value = whole_job_value(world, B, T)
+    stage = np.zeros(3)
+    nk = min(steps, 200)
+    for k in range(nk):
+        flush.fill_(float(k))
+        stage += np.array(dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info)[:3])
+    stage /= nk
+    mh = torch.tensor(m_np, dtype=torch.float32).pin_memory()
+    Hh = torch.empty_like(mh).pin_memory()
+    dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    ne = min(steps, 200)
+    e0 = time.perf_counter()
+    for _ in range(ne):
+        dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
+    Kx, Qy, npairs = info["Px"] // 2 + 1, info["Py"] // 2 + 1, info["npairs"]
+    field = B * L * 3 * ny * nx * 4
+    spec = B * L * 3 * Kx * ny * 8
+    tensor = Kx * npairs * 6 * Qy * 4
+    stage_bytes = [field + spec, 2 * spec + tensor, spec + field]
+    r8 = "8" if info["Px"] == 512 else ""
+    col = "k_columns_fused"
+    if info["path"] == 5:
+        col = "k_columns_ring8" if L <= 11 else "k_columns_fused8"
+    names = ["k_rows_forward" + r8, col, "k_rows_inverse" + r8]
+    dom = int(np.argmax(stage))
+    peak = float(peaks.get("hbm_gbs") or HBM_FALLBACK_GBS)
+    achieved = stage_bytes[dom] / (stage[dom] * 1e-3) / 1e9
+    out = {"workload": desc, "nx": nx, "ny": ny, "layers": L, "batch": B,
+           "l2": "256 MB buffer written between timed steps (cold L2 per step)", "steps": steps,
+           "value": value, "unit": "evals/s", "ms_per_step": T, "gcell_layers_per_s": nx * ny * L * value / 1e9,
+           "hbm_frac_min_bytes": ((2 * field + tensor) / (T * 1e-3) / 1e9) / peak,
+           "kernels_ms": dict(zip(names, [float(v) for v in stage])),
+           "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                        "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": recorded_traffic(names[dom]),
+                        "algorithmic_bytes": stage_bytes[dom]},
+           "e2e": {"value": whole_job_value(world, B, e2e_s * 1e3), "unit": "evals/s",
+                   "h2d_bytes_per_step": field, "d2h_bytes_per_step": field},
+           "plan_create_s": plan_s, "rel_l2_vs_oracle": None, "cpu_baseline": None}
+    if rank == 0 and with_oracle:
+        Khat = oracle_setup(c, th)
+        times, H_ref = oracle_timed(Khat, m_np, Ms, args.cpu_budget, 1000)
+        out["cpu_baseline"] = {"value": B / float(np.mean(times)), "unit": "evals/s", "cores": 1, "kind": "oracle",
+                               "sample": "%d whole evaluations of the workload, oracle float64 hybrid (numpy FFT, "
+                                         "single thread), tensor set-up not timed" % len(times)}
+        out["rel_l2_vs_oracle"] = float(np.linalg.norm(H.double().cpu().numpy() - H_ref) / np.linalg.norm(H_ref))
+    plan.close()
+    return out
+
+
+def batched_measurement(steps, peaks, n=512, layers=64, paths=(4, 6, 3)):
     """512 x 512 cells (n x n if given), 64 layers, 16 states per apply: the
     split-precision contraction on the tcgen05 tensor cores (path 6, the plan's
-    default) and with warp-level MMAs (path 4), against the same products on
-    the FP32 cores (path 3); same plan, same data movement."""
+    default), with warp-level MMAs (path 4) and the same products on the FP32
+    cores (path 3); same plan, same data movement."""
     import numpy as np
     import torch
 
@@ -305,7 +553,9 @@ def batched_measurement(steps, peaks, n=512, layers=64):
                        "states per apply; inputs (%.2f GB)" % (nx, ny, L, B * L * 3 * nx * ny * 4 / 1e9),
            "plan_create_s": build_s}
     fields = {}
-    for path, name in ((4, "tensor_cores_3xtf32"), (6, "tcgen05_3xtf32"), (3, "fp32_cores")):
+    names = {4: "tensor_cores_3xtf32", 6: "tcgen05_3xtf32", 3: "fp32_cores"}
+    for path in paths:
+        name = names[path]
         dm.demag_plan_set_path(plan.handle, path)
         info = dm.demag_plan_info(plan.handle)
         dm.demag_apply(plan.handle, m, inputs.MS_DEFAULT, H, info=info)
@@ -319,26 +569,168 @@ def batched_measurement(steps, peaks, n=512, layers=64):
                                     "contraction": float(st[4]), "columns_inverse": float(st[5]),
                                     "rows_inverse": float(st[2])},
                      "contraction_tflops_useful": flops / (st[4] * 1e-3) / 1e12}
-    tf32_peak = peaks.get("bf16_tflops", 1894.6) * (1.1 / 2.25)
+    tf32_peak = float(peaks.get("bf16_tflops", 1894.6)) * (1.1 / 2.25)
     for name in ("tensor_cores_3xtf32", "tcgen05_3xtf32"):
+        if name not in out:
+            continue
         tc = out[name]
-        tc["roofline"] = {"bound": "tensor", "achieved": 3 * tc["contraction_tflops_useful"],
-                          "peak": tf32_peak, "unit": "TFLOP/s",
-                          "frac": 3 * tc["contraction_tflops_useful"] / tf32_peak,
-                          "note": "TF32 issue rate (3 passes per useful flop) against the measured bf16 "
-                                  "burst peak x nominal tf32/bf16 ratio (1.1/2.25)"}
-    tc = out["tcgen05_3xtf32"]
-    d = fields[4] - fields[3]
-    out["rel_l2_between_variants"] = float(torch.linalg.vector_norm(d.double()) /
-                                           torch.linalg.vector_norm(fields[3].double()))
-    out["rel_l2_tcgen05_vs_fp32_cores"] = float(torch.linalg.vector_norm((fields[6] - fields[3]).double()) /
-                                                torch.linalg.vector_norm(fields[3].double()))
-    out["speedup_tensor_vs_fp32_cores"] = out["fp32_cores"]["ms_per_apply"] / tc["ms_per_apply"]
+        tc["tensor_pipe"] = {"bound": "tensor", "achieved": 3 * tc["contraction_tflops_useful"],
+                             "peak": tf32_peak, "unit": "TFLOP/s",
+                             "frac": 3 * tc["contraction_tflops_useful"] / tf32_peak,
+                             "note": "TF32 issue rate (3 passes per useful flop) against the measured bf16 burst "
+                                     "peak x nominal tf32/bf16 ratio (1.1/2.25)"}
+    if 3 in fields:
+        ref = fields[3].double()
+        for p in fields:
+            if p != 3:
+                out["rel_l2_%s_vs_fp32_cores" % names[p]] = float(
+                    torch.linalg.vector_norm(fields[p].double() - ref) / torch.linalg.vector_norm(ref))
+        if 6 in fields:
+            out["speedup_tcgen05_vs_fp32_cores"] = out["fp32_cores"]["ms_per_apply"] / \
+                out["tcgen05_3xtf32"]["ms_per_apply"]
     plan.close()
     return out
 
 
-def gradient_measurement(steps=20):
+def headline_measurement(args, world, rank, dist, peaks):
+    """The headline: 512 x 512 x 64 layers x 16 states, split-precision plan on
+    its default path (tcgen05 contraction)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import inputs
+    c, th, desc = headline_workload()
+    nx, ny, L, B = c["nx"], c["ny"], len(th), c["batch"]
+    Ms = inputs.MS_DEFAULT
+    m_np = inputs.random_unit_vectors((B, L, ny, nx), seed=rank_seed(rank))
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    plan_s = time.perf_counter() - t0
+    info = plan.info
+    m = torch.tensor(m_np, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(m)
+    run = lambda: dm.demag_apply(plan.handle, m, Ms, H, stream, info)  # noqa: E731
+    for _ in range(max(args.warmup, 3)):
+        run()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms = time_steps(run, args.steps, stream)
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    T = max_over_ranks(float(step_ms.mean()), dist, "cuda")
+    value = whole_job_value(world, B, T)
+    nk = min(args.steps, 10)
+    stage = np.mean([dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info) for _ in range(nk)], axis=0)
+    kernels_ms = [float(stage[0]), float(stage[3]), float(stage[4]), float(stage[5]), float(stage[2])]
+    names = split_stage_names(info)
+    sbytes, field, tensor = split_stage_bytes(info, B)
+    dom = int(np.argmax(kernels_ms))
+    peak = float(peaks.get("hbm_gbs") or HBM_FALLBACK_GBS)
+    achieved = sbytes[dom] / (kernels_ms[dom] * 1e-3) / 1e9
+    flops = 36.0 * L * L * B * (nx + 1) * (2 * ny)
+    tf32_peak = float(peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0) * (1.1 / 2.25)
+    H_gpu = H.clone()
+    # end to end: pinned host buffers, the kernels read m and write H over the host link
+    mh = torch.from_numpy(m_np.astype(np.float32)).pin_memory()
+    Hh = torch.empty_like(mh).pin_memory()
+    dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    ne = min(args.steps, 10)
+    e0 = time.perf_counter()
+    for _ in range(ne):
+        dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
+    e2e_match = bool(torch.equal(Hh, H_gpu.cpu()))
+    del mh, Hh
+    plan.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": T, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 FFTs, 3xTF32 contraction with f32 accumulate", "data": "synthetic",
+        "config": headline_config(c, th, desc, world, info),
+        "gcell_layers_per_s": nx * ny * L * value / 1e9,
+        "hbm_frac_min_bytes": ((2 * field + tensor) / (T * 1e-3) / 1e9) / peak,
+        "kernels_ms": dict(zip(names, kernels_ms)),
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                     "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback", "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(names[dom]),
+                     "algorithmic_bytes": sbytes[dom]},
+        "contraction_tensor_pipe": {"kernel": names[2], "useful_tflops": flops / (kernels_ms[2] * 1e-3) / 1e12,
+                                    "issued_tflops_3_passes": 3 * flops / (kernels_ms[2] * 1e-3) / 1e12,
+                                    "peak_tf32_tflops": tf32_peak,
+                                    "frac": 3 * flops / (kernels_ms[2] * 1e-3) / 1e12 / tf32_peak,
+                                    "note": "sustained bf16 peak x nominal tf32/bf16 ratio (1.1/2.25)"},
+        "e2e": {"value": whole_job_value(world, B, e2e_s * 1e3), "unit": "evals/s",
+                "h2d_bytes_per_step": field, "d2h_bytes_per_step": field,
+                "how": "demag_apply_host on pinned buffers (kernels read m and write H over NVLink-C2C), "
+                       "synchronised every step", "field_equals_device_run": e2e_match},
+        "gpu_launches": 5 * args.steps,
+        "plan_create_s": plan_s,
+        "wall_s_timed_loop": wall,
+    }
+    return line, m_np, H_gpu
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1910_07054_gb300 import inputs
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks = load_peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    line, m_np, H_gpu = headline_measurement(args, world, rank, dist, peaks)
+    line["clocks"] = clocks.stop()
+
+    extras = {}
+    if not args.no_extras:
+        extras["mram256"] = mram_block(args, world, rank, dist, peaks, with_oracle=not args.no_cpu)
+        if world == 1:
+            extras["split_variants"] = batched_measurement(3, peaks, paths=(4, 3))
+            extras["gradient"] = gradient_measurement(with_oracle=not args.no_parity)
+            extras["surrogate"] = surrogate_measurement()
+    if rank == 0:
+        c, th, _ = headline_workload()
+        L = len(th)
+        need_pk = (not args.no_parity) or (world == 1 and not args.no_cpu)
+        pk = headline_pair_kernels(c, th) if need_pk else None
+        if not args.no_parity or (world == 1 and not args.no_cpu):
+            t_s, H_ref = headline_oracle_sample(pk, m_np[0], inputs.MS_DEFAULT)
+            H_s = H_gpu[0, SAMPLE_TARGET].double().cpu().numpy()
+            line["rel_l2_vs_oracle"] = float(np.linalg.norm(H_s - H_ref) / np.linalg.norm(H_ref))
+            line["rel_l2_sample"] = "target layer %d of state 0 against the float64 oracle (Eq. FFT_v2 pair by " \
+                                    "pair)" % SAMPLE_TARGET
+            if world == 1 and not args.no_cpu:
+                line["cpu_baseline"] = {
+                    "value": 1.0 / (L * t_s), "unit": "evals/s", "cores": 1, "kind": "oracle",
+                    "sample": "one target layer (%d) of one state: oracle float64 hybrid_targets (numpy FFT, "
+                              "single thread) over the 64 source layers in %.1f s; evals/s = 1 / (64 x sample); "
+                              "pair kernels of the target row evaluated beforehand, not timed" % (SAMPLE_TARGET, t_s)}
+                if not args.no_allcore:
+                    line["cpu_baseline_all_cores"] = headline_oracle_allcore(pk, m_np, inputs.MS_DEFAULT, L)
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def gradient_measurement(steps=20, with_oracle=True):
     """The differentiation workload (256 x 256 cells of 2 nm, 10 layers with
     t ~ U[0.7, 4] nm, seed 0, one random state): the adjoint apply A^T gH
     (dH/dM) and d<H_z of layer 4>/d(thickness of layer 4), float plan.  The
@@ -354,7 +746,8 @@ def gradient_measurement(steps=20):
     nx, ny, L, layer = c["nx"], c["ny"], len(th), 3
     plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_FP32)
     info = plan.info
-    m = torch.tensor(inputs.random_unit_vectors((1, L, ny, nx), seed=0), dtype=torch.float32, device="cuda")
+    m_np = inputs.random_unit_vectors((1, L, ny, nx), seed=0)
+    m = torch.tensor(m_np, dtype=torch.float32, device="cuda")
     gH = torch.zeros_like(m)
     gH[0, layer, 2] = 1.0 / (nx * ny)
     gm = torch.empty_like(m)
@@ -376,11 +769,25 @@ def gradient_measurement(steps=20):
         g = dm.demag_thickness_grad(plan.handle, m, gH, inputs.MS_DEFAULT, layer, info=info)
     again_ms = (time.perf_counter() - t0) / steps * 1e3
     plan.close()
+    ref = None
+    if with_oracle:
+        # central difference (step 1e-4 nm) of the oracle's float64 mean H_z of
+        # the layer, Eq. FFT_v2 for that target layer only
+        from oracle import demag as odm
+        from oracle import newell as onw
+        h, vals = 1e-4, []
+        for sgn in (1.0, -1.0):
+            t = np.array(th)
+            t[layer] += sgn * h
+            pk = lambda i, j, t=t: onw.pair_kernel(nx, ny, c["dx"], c["dy"], t, i, j)  # noqa: E731
+            vals.append(float(odm.hybrid_targets(pk, m_np[0], inputs.MS_DEFAULT, [layer])[layer][2].mean()))
+        ref = (vals[0] - vals[1]) / (2 * h)
     return {"workload": "256x256 cells of 2x2 nm, 10 layers (t ~ U[0.7, 4] nm, seed 0), 1 random state, "
                         "float plan; d<H_z of layer 4>/dt_4 (1-based)",
             "adjoint_apply_ms": adj_ms, "adjoint_evals_per_s": 1e3 / adj_ms,
             "thickness_grad_first_s": first_s, "thickness_grad_cached_ms": again_ms,
-            "dhz_dt": float(g)}
+            "dhz_dt": float(g), "dhz_dt_oracle_central_difference": ref,
+            "dhz_dt_rel_err": None if ref is None else abs(float(g) - ref) / abs(ref)}
 
 
 def surrogate_measurement():
@@ -415,174 +822,19 @@ def surrogate_measurement():
             "surrogate_final_t_nm": su[-1][0]}
 
 
-def run_ours(args):
-    import numpy as np
-    import torch
-
-    import paper_1910_07054_gb300 as dm
-    from paper_1910_07054_gb300 import inputs
-
-    world, rank, local = dist_env()
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA GPU")
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    c, th, desc = workload()
-    nx, ny, L, B = c["nx"], c["ny"], len(th), c["batch"]
-    Ms = inputs.MS_DEFAULT
-    m_np = inputs.mram_magnetization(nx, ny, L, seed=rank_seed(rank), batch=B)
-    stream = torch.cuda.current_stream()
-
-    t0 = time.perf_counter()
-    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_FP32, max_batch=B)
-    plan_s = time.perf_counter() - t0
-    info = plan.info
-    m = torch.tensor(m_np, dtype=torch.float32, device="cuda")
-    H = torch.empty_like(m)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    for k in range(args.warmup):
-        flush.fill_(float(k))
-        dm.demag_apply(plan.handle, m, Ms, H, stream, info)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        starts[k].record(stream)
-        dm.demag_apply(plan.handle, m, Ms, H, stream, info)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    T = max_over_ranks(float(step_ms.mean()), dist, "cuda")
-    value = whole_job_value(world, B, T)
-
-    # per-kernel device times (same kernels, events between them, cold L2 each step)
-    nk = min(args.steps, 200)
-    stage = np.zeros(3)
-    for k in range(nk):
-        flush.fill_(float(k))
-        stage += np.array(dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info)[:3])
-    stage /= nk
-
-    # end to end through the host entry point (pinned buffers, copies included)
-    mh = torch.tensor(m_np, dtype=torch.float32).pin_memory()
-    Hh = torch.empty_like(mh).pin_memory()
-    ne = min(args.steps, 200)
-    dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
-    e0 = time.perf_counter()
-    for _ in range(ne):
-        dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
-    e2e_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
-    clk = clocks.stop()
-
-    # algorithmic bytes per launch (float32, B states)
-    Kx, Qy, npairs = info["Px"] // 2 + 1, info["Py"] // 2 + 1, info["npairs"]
-    field = B * L * 3 * ny * nx * 4
-    spec = B * L * 3 * Kx * ny * 8
-    tensor = Kx * npairs * 6 * Qy * 4
-    stage_bytes = [field + spec, 2 * spec + tensor, spec + field]
-    r8 = "8" if info["Px"] == 512 else ""
-    col = "k_columns_fused"
-    if info["path"] == 5:
-        col = "k_columns_ring8" if L <= 8 else "k_columns_fused8"
-    names = ["k_rows_forward" + r8, col, "k_rows_inverse" + r8]
-    dom = int(np.argmax(stage))
-    peak, peak_kind = measured_hbm_peak()
-    achieved = stage_bytes[dom] / (stage[dom] * 1e-3) / 1e9
-    traffic = recorded_traffic(names[dom])
-
-    extras = {}
-    if world == 1 and not args.no_extras:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
-                os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as fh:
-            try:
-                peaks = json.load(fh)
-            except ValueError:
-                peaks = {}
-        extras["batched"] = batched_measurement(3, peaks)
-        extras["gradient"] = gradient_measurement()
-        extras["surrogate"] = surrogate_measurement()
-
-    line = None
-    if rank == 0:
-        H_host = H.double().cpu().numpy()
-        rel = None
-        cpu = None
-        want_cpu = world == 1 and not args.no_cpu
-        if want_cpu or not args.no_parity:
-            Khat = oracle_setup(c, th)
-            if want_cpu:
-                times, H_ref = oracle_timed(Khat, m_np, Ms, args.cpu_budget, 1000)
-                cpu = {"value": B / float(np.mean(times)), "unit": "evals/s", "cores": 1, "kind": "oracle",
-                       "sample": "%d whole evaluations of the workload, oracle float64 hybrid (numpy "
-                                 "FFT, single thread), tensor set-up not timed" % len(times)}
-            else:
-                from oracle import demag as odm
-                H_ref = odm.hybrid(None, m_np, Ms, Khat=Khat)
-            if not args.no_parity:
-                rel = float(np.linalg.norm(H_host - H_ref) / np.linalg.norm(H_ref))
-        min_bytes = 2 * field + tensor
-        line = {
-            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": T, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "nx": nx, "ny": ny, "layers": L, "batch_per_gpu": B,
-                       "padded_fft": [info["Px"], info["Py"]],
-                       "l2": "256 MB buffer written between timed steps (cold L2 per step)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "gcell_layers_per_s": nx * ny * L * value / 1e9,
-            "rel_l2_vs_oracle": rel,
-            "hbm_frac_min_bytes": (min_bytes / (T * 1e-3) / 1e9) / peak,
-            "kernels_ms": dict(zip(names, [float(v) for v in stage])),
-            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                         "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "algorithmic_bytes": stage_bytes[dom]},
-            "cpu_baseline": cpu,
-            "e2e": {"value": whole_job_value(world, B, e2e_s * 1e3), "unit": "evals/s", "h2d_bytes_per_step": field,
-                    "d2h_bytes_per_step": field},
-            "gpu_launches": 3 * args.steps,
-            "clocks": clk,
-            "plan_create_s": plan_s,
-            "batched": extras.get("batched"),
-            "gradient": extras.get("gradient"),
-            "surrogate": extras.get("surrogate"),
-            "wall_s_timed_loop": wall,
-        }
-    plan.close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    if line is not None:
-        print(json.dumps(line), flush=True)
-
-
 def main():
     args = parse_args()
     if args.batched_only:
-        peaks = {}
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-                peaks = json.load(fh)
-        print(json.dumps(batched_measurement(max(args.steps, 1), peaks, args.batched_n, args.batched_layers)),
+        print(json.dumps(batched_measurement(max(args.steps, 1), load_peaks(), args.batched_n, args.batched_layers)),
               flush=True)
         return
     if args.grad_only:
-        print(json.dumps(gradient_measurement()), flush=True)
+        print(json.dumps(gradient_measurement(with_oracle=not args.no_parity)), flush=True)
+        return
+    if args.mram_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(mram_block(args, 1, 0, None, load_peaks(), with_oracle=not args.no_cpu)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

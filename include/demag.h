@@ -76,11 +76,15 @@ const char *demag_last_error(void);
  * the plan tensor through shared memory with asynchronous bulk copies.  Each
  * of their waits on a copy is bounded (about one second); a wait that runs out
  * is counted on the device and the kernel completes without hanging, but the
- * field it wrote is then invalid.  This call synchronises the current device,
- * stores the count accumulated since the previous call in *count and clears
- * it.  Returns DEMAG_EINVAL for a NULL count, DEMAG_ECUDA if the counter
- * cannot be read.  A non-zero count means some apply since the previous call
- * produced an invalid field.
+ * field it wrote is then invalid.  This call synchronises the current device
+ * and stores in *count the timeouts on that device not yet reported, by this
+ * call or by a synchronising entry point (demag_apply_host, demag_apply_timed,
+ * demag_thickness_grad: those return DEMAG_ECUDA when they find any).  The
+ * asynchronous entry points (demag_apply, demag_apply_adjoint,
+ * demag_apply_dthickness, demag_apply_static) cannot report a timeout in
+ * their status; poll this call after them.  Returns DEMAG_EINVAL for a NULL
+ * count, DEMAG_ECUDA if the counters cannot be read.  A non-zero count means
+ * some apply since the previous report produced an invalid field.
  */
 demag_status demag_wait_timeouts(unsigned long long *count);
 
@@ -153,6 +157,10 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
  *   H      DEVICE, same shape and type as m, written (must not alias m)
  *   B      1 <= B <= max_batch of the plan
  *   stream stream to order the work on (asynchronous)
+ *
+ * The status reports argument and launch errors only; a bounded device wait
+ * that gave up during the kernels (see demag_wait_timeouts) is reported by
+ * demag_wait_timeouts or by the next synchronising entry point.
  */
 demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, int B,
                          void *stream);
@@ -232,7 +240,7 @@ demag_status demag_apply_dthickness(demag_plan_t plan, const void *m, double Ms,
  *
  *   m, gH  DEVICE, [B][L][3][ny][nx]
  *   out    HOST, one double, written
- * Synchronises `stream`.
+ * Synchronises `stream`; reports bounded-wait timeouts like demag_apply_host.
  */
 demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *gH, double Ms, int B,
                                   int layer, double *out, void *stream);
@@ -245,7 +253,10 @@ demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *
  * transfers with the row transforms; other host memory is copied through the
  * plan's device staging buffers (allocated on first use) before and after
  * demag_apply.  Either way the call synchronises the stream before it
- * returns and the field is identical.
+ * returns and the field is identical.  Returns DEMAG_ECUDA (message in
+ * demag_last_error) if a bounded device wait on this device gave up since the
+ * timeouts were last reported (see demag_wait_timeouts): the field is then
+ * invalid.
  *
  *   m, H   HOST, [B][L][3][ny][nx] of the plan's real type
  *   other arguments as in demag_apply
@@ -265,7 +276,8 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
  *     with nstage >= 6 on a plan running the split path (2, 3, 4) also
  *     [3] forward column transforms, [4] layer contraction, [5] inverse
  *     column transforms (the parts of [1]); zero otherwise.
- * Other arguments as in demag_apply.
+ * Other arguments as in demag_apply.  Reports bounded-wait timeouts like
+ * demag_apply_host.
  */
 demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void *H, int B,
                                void *stream, float *stage_ms, int nstage);
@@ -339,8 +351,12 @@ demag_status demag_tensor_points(int n, const double *geom, double *out, void *s
  *   tensor     DEVICE, 16-byte aligned, layout and values exactly as written
  *              by demag_plan_tensor for a plan of the same nx, ny, thickness,
  *              precision (any max_batch)
+ *   tensor_bytes  size of tensor in bytes: must equal the size
+ *              demag_plan_tensor writes for such a plan
+ *              ((Px/2+1) * npairs * 6 * QyS values), else DEMAG_EINVAL
  *   thickness  HOST, L layer thicknesses (same as for that plan)
- *   nx, ny, L, precision   as for demag_plan_create
+ *   nx, ny, L, precision   as for demag_plan_create (DEMAG_PREC_FP64 or
+ *              DEMAG_PREC_FP32)
  *   m, Ms, H, B, stream    as for demag_apply (no max_batch: the scratch size
  *              is the limit)
  *
@@ -348,15 +364,17 @@ demag_status demag_tensor_points(int n, const double *geom, double *out, void *s
  * twiddle tables and an L*L ratio table; a request above 32 MiB returns
  * DEMAG_EUNSUPPORTED with the required size in demag_last_error().
  * The first call on a device looks up the array's device address (a one-time
- * set-up per device); make that first call before any stream capture.  All
- * calls on a device share the array: calls whose GPU work overlaps (other
- * streams, other host threads) race on it; calls ordered on one stream do
- * not.  Nothing in it needs clearing between calls.  The copies of the small
- * tables from host memory synchronise the stream with earlier work on it.
+ * set-up per device, repeated after a call on that device fails); make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: calls whose GPU work overlaps (other streams, other host threads)
+ * race on it; calls ordered on one stream do not.  Every call recomputes the
+ * small tables on the device and overwrites the workspace it reads, so
+ * nothing in the array needs clearing between calls.  The call copies nothing
+ * from host memory; the thicknesses travel as a kernel argument.
  */
-demag_status demag_apply_static(const void *tensor, const double *thickness, int nx, int ny, int L,
-                                int precision, const void *m, double Ms, void *H, int B,
-                                void *stream);
+demag_status demag_apply_static(const void *tensor, size_t tensor_bytes, const double *thickness,
+                                int nx, int ny, int L, int precision, const void *m, double Ms, void *H,
+                                int B, void *stream);
 
 /*
  * demag_tensor_points_dt - the tensor of demag_tensor_points and its

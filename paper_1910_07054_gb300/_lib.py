@@ -70,7 +70,7 @@ def lib():
     L.demag_thickness_grad.restype = i
     L.demag_tensor_points_dt.argtypes = [i, vp, vp, vp, vp]
     L.demag_tensor_points_dt.restype = i
-    L.demag_apply_static.argtypes = [vp, dp, i, i, i, i, vp, d, vp, i, vp]
+    L.demag_apply_static.argtypes = [vp, ctypes.c_size_t, dp, i, i, i, i, vp, d, vp, i, vp]
     L.demag_apply_static.restype = i
     f = ctypes.c_float
     L.demag_mlp_param_count.argtypes = [i, i, i]
@@ -273,14 +273,19 @@ def demag_tensor_points(geom, out, stream=None):
 def demag_apply_static(tensor, thickness, nx, ny, precision, m, Ms, H, stream=None):
     """demag_apply without device allocation: tensor is the device copy written by
     demag_plan_tensor; the library's fixed scratch array holds the workspace."""
+    import torch
     info = {"L": len(thickness), "nx": nx, "ny": ny, "precision": precision}
+    want = torch.float64 if precision == PREC_FP64 else torch.float32
+    if tensor.dtype != want or not tensor.is_cuda or not tensor.is_contiguous():
+        raise TypeError("tensor must be a contiguous CUDA %s tensor for this precision" % want)
     B = _field_check(m, info, "m")
     if _field_check(H, info, "H") != B or H.shape != m.shape:
         raise ValueError("H must have the shape of m")
     th = (ctypes.c_double * len(thickness))(*[float(t) for t in thickness])
-    _check(lib().demag_apply_static(ctypes.c_void_p(tensor.data_ptr()), th, int(nx), int(ny),
-                                    len(thickness), int(precision), ctypes.c_void_p(m.data_ptr()),
-                                    float(Ms), ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)),
+    _check(lib().demag_apply_static(ctypes.c_void_p(tensor.data_ptr()), tensor.numel() * tensor.element_size(),
+                                    th, int(nx), int(ny), len(thickness), int(precision),
+                                    ctypes.c_void_p(m.data_ptr()), float(Ms), ctypes.c_void_p(H.data_ptr()),
+                                    int(B), _stream(stream)),
            "demag_apply_static")
     return H
 

@@ -1,6 +1,7 @@
 // C ABI of libdemag: plan lifecycle, argument checks and error reporting.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <cstdio>
 #include <cstring>
@@ -61,7 +62,46 @@ static void free_plan(demag_plan *p) {
     cudaFree(p->d_dtensor);
     cudaFree(p->d_dH);
     cudaFree(p->d_dot);
+    if (p->h_timeouts) cudaFreeHost(p->h_timeouts);
     delete p;
+}
+
+// ---- bounded-wait timeouts ------------------------------------------------
+// The kernels that stream the tensor with asynchronous copies count every
+// bounded wait that gave up in two device counters that only grow.  The host
+// remembers, per device, how much of each count it has already reported; a
+// synchronising entry point (or demag_wait_timeouts) reports the rest.
+static std::mutex g_timeout_mu;
+static unsigned g_timeouts_seen[64][2];
+
+// Counts new since the last report on this device; updates the record.
+static unsigned long long take_new_timeouts(int dev, const unsigned *now) {
+    if (dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(g_timeout_mu);
+    unsigned long long n = 0;
+    for (int k = 0; k < 2; ++k)
+        if (now[k] > g_timeouts_seen[dev][k]) {
+            n += now[k] - g_timeouts_seen[dev][k];
+            g_timeouts_seen[dev][k] = now[k];
+        }
+    return n;
+}
+
+// Enqueues on `st` the copies of both counters into the plan's pinned words.
+static cudaError_t enqueue_timeout_read(demag_plan *p, cudaStream_t st) {
+    cudaError_t e = read_wait_timeouts(&p->h_timeouts[0], st);
+    if (e == cudaSuccess) e = read_tc_timeouts(&p->h_timeouts[1], st);
+    return e;
+}
+
+// After `st` was synchronised behind enqueue_timeout_read: DEMAG_ECUDA if a
+// bounded wait gave up since the counts were last reported.
+static demag_status timeout_status(demag_plan *p, const char *where) {
+    const unsigned long long n = take_new_timeouts(p->device, p->h_timeouts);
+    if (n == 0) return DEMAG_OK;
+    return fail(DEMAG_ECUDA, std::string(where) + ": " + std::to_string(n) +
+                                 " bounded device wait(s) gave up (an asynchronous tensor copy did not "
+                                 "complete within the limit); the result is invalid");
 }
 
 // Device allocation that records the failure.
@@ -250,11 +290,14 @@ demag_status demag_selftest_bounded_wait(long long limit_cycles, void *stream) {
 
 demag_status demag_wait_timeouts(unsigned long long *count) {
     if (!count) return fail(DEMAG_EINVAL, "count is NULL");
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-    const unsigned n = take_wait_timeouts(), n5 = take_tc_timeouts();
-    if (n == ~0u || n5 == ~0u) return fail(DEMAG_ECUDA, "cannot read the wait-timeout counters");
-    *count = (unsigned long long)n + n5;
+    int dev = 0;
+    DEMAG_CUDA(cudaGetDevice(&dev));
+    DEMAG_CUDA(cudaDeviceSynchronize());
+    unsigned now[2] = {0, 0};
+    DEMAG_CUDA(read_wait_timeouts(&now[0], 0));
+    DEMAG_CUDA(read_tc_timeouts(&now[1], 0));
+    DEMAG_CUDA(cudaStreamSynchronize(0));
+    *count = take_new_timeouts(dev, now);
     return DEMAG_OK;
 }
 
@@ -341,6 +384,11 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
         rc = dalloc(&p->d_spec2, split_workspace_bytes(L, max_batch, p->log2Px, p->log2Py, fp64),
                     "column workspace");
     if (rc == DEMAG_OK) rc = dalloc(&p->d_tscale, (size_t)2 * L * real, "layer scales");
+    if (rc == DEMAG_OK && (e = cudaHostAlloc((void **)&p->h_timeouts, 2 * sizeof(unsigned), cudaHostAllocDefault)) !=
+                              cudaSuccess) {
+        p->h_timeouts = nullptr;
+        rc = cuda_fail(e, "cudaHostAlloc(timeout counters)");
+    }
     if (rc == DEMAG_OK) {
         // t_j / t_i for target i, source j (reciprocity of the stored pairs)
         std::vector<double> r64((size_t)L * L);
@@ -439,6 +487,7 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
     ApplyArgs a = apply_args(plan, Ms, B);
     if (inner) a.inner_ev = ev + kApplyStages + 1;
     if (e == cudaSuccess) e = launch_apply(a, m, H, plan->precision == DEMAG_PREC_FP64, st, ev);
+    if (e == cudaSuccess) e = enqueue_timeout_read(plan, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (int k = 0; e == cudaSuccess && k < kApplyStages; ++k)
         e = cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]);
@@ -448,7 +497,7 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
     for (int k = kApplyStages; k < nstage && !inner; ++k) stage_ms[k] = 0.0f;
     for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(e, "demag_apply_timed");
-    return DEMAG_OK;
+    return timeout_status(plan, "demag_apply_timed");
 }
 
 demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, void *H_host, int B,
@@ -468,8 +517,9 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
         cudaError_t e = launch_apply(apply_args(plan, Ms, B), am.devicePointer, ah.devicePointer,
                                      plan->precision == DEMAG_PREC_FP64, st);
         if (e != cudaSuccess) return cuda_fail(e, "demag_apply_host kernels");
+        DEMAG_CUDA(enqueue_timeout_read(plan, st));
         DEMAG_CUDA(cudaStreamSynchronize(st));
-        return DEMAG_OK;
+        return timeout_status(plan, "demag_apply_host");
     }
     if (!plan->d_stage_m) {
         const size_t full = plan->field_bytes_per_state * (size_t)plan->max_batch;
@@ -481,8 +531,9 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
                                  plan->precision == DEMAG_PREC_FP64, st);
     if (e != cudaSuccess) return cuda_fail(e, "demag_apply_host kernels");
     DEMAG_CUDA(cudaMemcpyAsync(H_host, plan->d_stage_H, bytes, cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(enqueue_timeout_read(plan, st));
     DEMAG_CUDA(cudaStreamSynchronize(st));
-    return DEMAG_OK;
+    return timeout_status(plan, "demag_apply_host");
 }
 
 demag_status demag_plan_set_path(demag_plan_t plan, int path) {
@@ -571,8 +622,9 @@ demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *
         k_dot<float><<<grid, 256, 0, st>>>((const float *)gH, (const float *)plan->d_dH, n, plan->d_dot);
     DEMAG_CUDA(cudaGetLastError());
     DEMAG_CUDA(cudaMemcpyAsync(out, plan->d_dot, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DEMAG_CUDA(enqueue_timeout_read(plan, st));
     DEMAG_CUDA(cudaStreamSynchronize(st));
-    return DEMAG_OK;
+    return timeout_status(plan, "demag_thickness_grad");
 }
 
 demag_status demag_tensor_points_dt(int n, const double *geom, double *out, double *dout,

@@ -845,11 +845,8 @@ cudaError_t launch_selftest_wait(long long limit, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-unsigned take_wait_timeouts() {
-    unsigned n = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&n, g_wait_timeouts8, sizeof(n)) != cudaSuccess) return ~0u;
-    if (n != 0) cudaMemcpyToSymbol(g_wait_timeouts8, &zero, sizeof(zero));
-    return n;
+cudaError_t read_wait_timeouts(unsigned *dst, cudaStream_t st) {
+    return cudaMemcpyFromSymbolAsync(dst, g_wait_timeouts8, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
 }
 
 bool cols512_supported(int log2Py, int L, bool fp64) {

@@ -521,11 +521,8 @@ cudaError_t launch_contract_tc5(const ApplyArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-unsigned take_tc_timeouts() {
-    unsigned n = 0, zero = 0;
-    if (cudaMemcpyFromSymbol(&n, g_tc_timeouts, sizeof(n)) != cudaSuccess) return ~0u;
-    if (n != 0) cudaMemcpyToSymbol(g_tc_timeouts, &zero, sizeof(zero));
-    return n;
+cudaError_t read_tc_timeouts(unsigned *dst, cudaStream_t st) {
+    return cudaMemcpyFromSymbolAsync(dst, g_tc_timeouts, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st);
 }
 
 }  // namespace demag

@@ -100,9 +100,9 @@ template <typename T>
 cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forward, cudaStream_t st);
 template <typename T>
 cudaError_t launch_cols512(const ApplyArgs &a, cudaStream_t st);
-// Bounded waits of the streamed column kernel that gave up since the last
-// call (the count is cleared); ~0u if the counter could not be read.
-unsigned take_wait_timeouts();
+// Bounded waits of the streamed column kernel that gave up: the device
+// counter only grows; this enqueues a copy of its value to *dst on `st`.
+cudaError_t read_wait_timeouts(unsigned *dst, cudaStream_t st);
 // One block whose single bounded wait cannot complete (gives up after `limit` cycles).
 cudaError_t launch_selftest_wait(long long limit, cudaStream_t st);
 
@@ -119,7 +119,8 @@ cudaError_t launch_rows1024(bool inverse, const void *src, void *dst, int nx, in
                             int log2tw, float out_scale, const void *layer_scale, int L, cudaStream_t st);
 bool tc5_supported(int L, int B, int npairs);
 cudaError_t launch_contract_tc5(const ApplyArgs &a, cudaStream_t st);
-unsigned take_tc_timeouts();
+// The same count for the tcgen05 contraction kernel.
+cudaError_t read_tc_timeouts(unsigned *dst, cudaStream_t st);
 
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);
@@ -156,6 +157,7 @@ struct demag_plan {
     double *d_dot = nullptr;      // reduction scratch
     void *d_stage_m = nullptr;    // staging for demag_apply_host
     void *d_stage_H = nullptr;
+    unsigned *h_timeouts = nullptr;  // pinned host copy of the two bounded-wait counters
     size_t tensor_bytes = 0, field_bytes_per_state = 0;
     int device = 0;
 };

@@ -57,7 +57,7 @@ def test_other_entry_points_reject_null_and_bad_sizes():
     assert lib.demag_apply(None, None, 1.0, None, 1, None) == 1
     assert lib.demag_apply_host(None, None, 1.0, None, 1, None) == 1
     assert lib.demag_apply_timed(None, None, 1.0, None, 1, None, None, 3) == 1
-    assert lib.demag_apply_static(None, None, 4, 4, 1, 1, None, 1.0, None, 1, None) == 1
+    assert lib.demag_apply_static(None, 0, None, 4, 4, 1, 1, None, 1.0, None, 1, None) == 1
     assert lib.demag_tensor_points(-1, None, None, None) == 1
     assert lib.demag_tensor_points(5, None, None, None) == 1
     assert lib.demag_plan_info(None, None) == 1

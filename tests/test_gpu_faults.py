@@ -74,3 +74,34 @@ def test_bounded_wait_gives_up_and_is_reported():
     assert dm.demag_wait_timeouts() == 0  # reading clears the count
     with pytest.raises(dm.DemagError):
         dm.demag_selftest_bounded_wait(0)
+
+
+def test_synchronising_call_reports_a_timeout_as_an_error():
+    """A bounded wait that gave up (here the self test's, with a short limit)
+    makes the next synchronising entry point return DEMAG_ECUDA instead of a
+    silently invalid field; the report is taken once, so the call after it
+    succeeds and demag_wait_timeouts has nothing left to report."""
+    from paper_1910_07054_gb300._lib import DEMAG_ECUDA
+    th = (1.0, 0.5)
+    m = inputs.random_unit_vectors((1, 2, 12, 20), seed=5).astype(np.float32)
+    plan = dm.Plan(20, 12, 2.0, 2.0, th, precision=dm.PREC_FP32)
+    mh = torch.tensor(m).pin_memory()
+    Hh = torch.empty_like(mh).pin_memory()
+    dm.demag_apply_host(plan.handle, mh, 1.0, Hh, info=plan.info)
+    ref = Hh.clone()
+    assert dm.demag_wait_timeouts() == 0
+    dm.demag_selftest_bounded_wait(1 << 16)
+    with pytest.raises(dm.DemagError) as ei:
+        dm.demag_apply_host(plan.handle, mh, 1.0, Hh, info=plan.info)
+    assert ei.value.status == DEMAG_ECUDA
+    assert "bounded device wait" in str(ei.value)
+    Hh.zero_()
+    dm.demag_apply_host(plan.handle, mh, 1.0, Hh, info=plan.info)
+    assert torch.equal(Hh, ref)
+    assert dm.demag_wait_timeouts() == 0
+    dm.demag_selftest_bounded_wait(1 << 16)
+    mt = mh.cuda()
+    with pytest.raises(dm.DemagError) as ei:
+        dm.demag_apply_timed(plan.handle, mt, 1.0, torch.empty_like(mt), info=plan.info)
+    assert ei.value.status == DEMAG_ECUDA
+    plan.close()

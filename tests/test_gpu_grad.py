@@ -235,3 +235,108 @@ def test_dthickness_on_512_point_transforms(nx, ny):
     plan.close()
     ref = odm.hybrid(onw.layer_dkernels(nx, ny, 2.0, 2.0, th, 1), m[0], 2.0)
     assert rel_l2(dH[0].cpu().numpy(), ref) < 1e-9
+
+
+# ---- float plans ---------------------------------------------------------------
+# The float kernels round every FFT stage and every contraction sum to float
+# (unit roundoff 6e-8); over the log2(512) = 9 butterfly stages of each of the
+# four transforms and the sum over L source layers the field carries a relative
+# error of a few 1e-7 (4e-7 measured on the 256 x 256 x 8 stack).  The adjoint
+# and the derivative field run the same kernels, so they are held to the float
+# field's bound, 1e-5 relative L2.  The derivative tensor is built in double and
+# stored in float (one more rounding per entry), which leaves that bound intact.
+FLOAT_TOL = 1e-5
+
+
+def _transposed_oracle(nx, ny, th, g, Ms):
+    K = reading_kernels(nx, ny, 2.0, 2.0, tuple(th))
+    KT = np.transpose(K[:, :, :, ::-1, ::-1], (1, 0, 2, 3, 4))  # KT[i, j](d) = K[j, i](-d)
+    return odm.hybrid(KT, g, Ms)
+
+
+@pytest.mark.parametrize("nx,ny,th,path", [
+    (200, 140, (1.0, 0.5, 2.0), 5),        # 512-point rows and the streamed-ring columns
+    (40, 24, (1.0, 0.6, 2.0, 0.9), 1),     # generic rows, fused columns
+    (40, 24, (1.0, 0.6, 2.0, 0.9), 2),     # generic rows, split columns
+])
+def test_float_adjoint_matches_oracle_transposed_convolution(nx, ny, th, path):
+    """A^T gH on float plans: the rows carry the source scales 1/t_j on input and
+    the target scales t_i on output (Sec. 3 reciprocity), in float."""
+    g = inputs.random_unit_vectors((1, len(th), ny, nx), seed=41)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_FP32)
+    if path != 5:
+        dm.demag_plan_set_path(plan.handle, path)
+        plan.info = dm.demag_plan_info(plan.handle)
+    assert plan.info["path"] == path
+    gm = _adjoint(plan, g, 2.0)[0]
+    plan.close()
+    assert rel_l2(gm, _transposed_oracle(nx, ny, th, g[0], 2.0)) < FLOAT_TOL
+
+
+def test_grad256_float_adjoint_matches_oracle():
+    """The differentiation workload (256 x 256 x 10) on a float plan: the
+    streamed-ring column kernel at 10 layers with the adjoint's layer scales."""
+    c = inputs.CONFIGS["grad256"]
+    th = tuple(inputs.thicknesses("grad256"))
+    g = inputs.random_unit_vectors((1, len(th), c["ny"], c["nx"]), seed=43)
+    plan = dm.Plan(c["nx"], c["ny"], c["dx"], c["dy"], th, precision=dm.PREC_FP32)
+    assert plan.info["path"] == 5
+    gm = _adjoint(plan, g, inputs.MS_DEFAULT)[0]
+    plan.close()
+    K = reading_kernels(c["nx"], c["ny"], c["dx"], c["dy"], th)
+    KT = np.transpose(K[:, :, :, ::-1, ::-1], (1, 0, 2, 3, 4))
+    assert rel_l2(gm, odm.hybrid(KT, g[0], inputs.MS_DEFAULT)) < FLOAT_TOL
+
+
+@pytest.mark.parametrize("nx,ny,th,layers", [
+    (10, 8, (1.0, 0.5, 2.0, 0.8), (0, 2, 3)),   # generic kernels
+    (200, 3, (1.0, 2.0), (1,)),                 # 512-point row kernels
+    (3, 140, (1.0, 2.0), (0, 1)),               # 512-point fused columns, all L^2 pairs
+])
+def test_float_dthickness_field_matches_oracle(nx, ny, th, layers):
+    """dH/dt_l on float plans against the oracle's derivative kernels
+    (_Float128 central differences of the exact tensor)."""
+    th = np.array(th)
+    m = inputs.random_unit_vectors((1, len(th), ny, nx), seed=47)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, tuple(th), precision=dm.PREC_FP32)
+    mt = torch.tensor(m, dtype=torch.float32, device="cuda")
+    for layer in layers:
+        dH = torch.empty_like(mt)
+        dm.demag_apply_dthickness(plan.handle, mt, 2.0, dH, layer, info=plan.info)
+        torch.cuda.synchronize()
+        ref = odm.hybrid(onw.layer_dkernels(nx, ny, 2.0, 2.0, th, layer), m[0], 2.0)
+        assert rel_l2(dH[0].double().cpu().numpy(), ref) < FLOAT_TOL, layer
+    plan.close()
+
+
+def _oracle_mean_top_hz(nx, ny, dx, th, m, Ms):
+    """Mean H_z of the top layer from the oracle (Eq. FFT_v2, target layer only,
+    double-precision reading of the tensor)."""
+    L = len(th)
+    pk = lambda i, j: onw.pair_kernel(nx, ny, dx, dx, th, i, j)  # noqa: E731
+    return odm.hybrid_targets(pk, m, Ms, [L - 1])[L - 1][2].mean()
+
+
+def test_grad256_float_thickness_gradient_matches_oracle_central_difference():
+    """d(mean H_z of the top layer)/d(thickness of layer 4, 1-based) on the
+    256 x 256 x 10 stack from a float plan, against a central difference (step
+    1e-4 nm) of the oracle's double-precision field.  The difference quotient
+    carries the oracle's field error (~1e-13 relative) divided by the step, far
+    below the float bound."""
+    c = inputs.CONFIGS["grad256"]
+    nx, ny, dx = c["nx"], c["ny"], c["dx"]
+    th = inputs.thicknesses("grad256")
+    L, layer, Ms = len(th), 3, inputs.MS_DEFAULT
+    m = inputs.random_unit_vectors((1, L, ny, nx), seed=0)
+    plan = dm.Plan(nx, ny, dx, dx, tuple(th), precision=dm.PREC_FP32)
+    mt = torch.tensor(m, dtype=torch.float32, device="cuda")
+    gH = torch.zeros_like(mt)
+    gH[0, -1, 2] = 1.0 / (nx * ny)
+    g = dm.demag_thickness_grad(plan.handle, mt, gH, Ms, layer, info=plan.info)
+    plan.close()
+    h = 1e-4
+    tp, tm = th.copy(), th.copy()
+    tp[layer] += h
+    tm[layer] -= h
+    fd = (_oracle_mean_top_hz(nx, ny, dx, tp, m[0], Ms) - _oracle_mean_top_hz(nx, ny, dx, tm, m[0], Ms)) / (2 * h)
+    assert abs(g - fd) <= FLOAT_TOL * abs(fd), (g, fd)
