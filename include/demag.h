@@ -55,10 +55,16 @@ typedef enum {
 typedef enum {
     DEMAG_PREC_FP64 = 0,       /* FFTs and layer contraction in double          */
     DEMAG_PREC_FP32 = 1,       /* FFTs and layer contraction in float           */
-    DEMAG_PREC_SPLIT_TF32 = 2  /* float FFTs; the contraction as dense products
+    DEMAG_PREC_SPLIT_TF32 = 2, /* float FFTs; the contraction as dense products
                                   on the tensor cores in three TF32 passes
                                   (a_hi b_hi + a_hi b_lo + a_lo b_hi, float
-                                  accumulation), for batches of states        */
+                                  accumulation), for batches of states; each
+                                  product within 2^-21 of exact              */
+    DEMAG_PREC_SPLIT_BF16 = 3  /* the same with three BF16 passes (hi and lo
+                                  each 8 significant bits): half the tensor-
+                                  core instructions of SPLIT_TF32, each product
+                                  within about 3 * 2^-18 of exact (field about
+                                  2e-6 relative L2 from the double oracle)   */
 } demag_precision;
 
 typedef struct demag_plan *demag_plan_t;
@@ -128,8 +134,8 @@ demag_status demag_debug_fail_alloc(int after);
  *   dx, dy     in-plane cell edges, > 0 and finite
  *   thickness  HOST array of L layer thicknesses, each > 0 and finite
  *   L          number of layers, 1 <= L <= 256
- *   precision  a demag_precision value; DEMAG_PREC_SPLIT_TF32 needs
- *              (6 L^2 + 12 L B + 12 L B) floats (L padded to 16, B to 8)
+ *   precision  a demag_precision value; DEMAG_PREC_SPLIT_TF32 and
+ *              DEMAG_PREC_SPLIT_BF16 need (6 L^2 + 12 L B + 12 L B) floats (L padded to 16, B to 8)
  *              within 220 KB of shared memory, and its tensor is stored in
  *              the layout [kx][u][component][pair] (see demag_plan_tensor)
  *   max_batch  largest batch B later passed to demag_apply, >= 1
@@ -175,21 +181,25 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
  *   path 2: column FFT, contraction and inverse column FFT as three kernels
  *           through a [Kx][Py][B][L][3] complex workspace (allocated here on
  *           first use).
- *   path 3: (DEMAG_PREC_SPLIT_TF32 plans) column kernels of path 2 with the
+ *   path 3: (split-precision plans) column kernels of path 2 with the
  *           contraction as dense L x L by L x B products on the FP32 cores.
- *   path 4: (DEMAG_PREC_SPLIT_TF32 plans) the same products on the tensor
+ *   path 4: (split-precision plans) the same products on the tensor
  *           cores in three TF32 passes (warp-level m16n8k8 TF32 MMAs, two
  *           blocks per SM).
  *   path 5: (reported, not selectable otherwise) the fused column kernel with
  *           the radix-8 512-point transforms, chosen by demag_plan_create
  *           when Py = 512 and the columns fit; its tensor is stored in
  *           natural folded-ky order, so such a plan runs path 5 only.
- *   path 6: (DEMAG_PREC_SPLIT_TF32 plans with even L <= 64 and max_batch <=
- *           16, their default) the same products on the tcgen05 tensor cores:
- *           3xTF32, the tensor operand built in tensor memory, accumulators in
- *           tensor memory, one persistent block per SM.
+ *   path 6: (split-precision plans with even L <= 64 and max_batch <= 16;
+ *           the default of DEMAG_PREC_SPLIT_TF32 plans) the same products on
+ *           the tcgen05 tensor cores: 3xTF32, the tensor operand built in
+ *           tensor memory, accumulators in tensor memory, one persistent
+ *           block per SM.
+ *   path 7: (the same plans; the default of DEMAG_PREC_SPLIT_BF16 plans) path
+ *           6 with 3xBF16 operands (kind::f16, K = 16 per instruction).
  *   path 0: the default choice of demag_plan_create (5 or 1 when it fits,
- *           else 2; for DEMAG_PREC_SPLIT_TF32 6 when it holds the plan, else 4).
+ *           else 2; for split-precision plans 6 (TF32) or 7 (BF16) when it
+ *           holds the plan, else 4).
  * All paths compute the same field (Eq. FFT_v2); this entry point exists to
  * test and time them against each other.  Errors: DEMAG_EINVAL, DEMAG_ENOMEM,
  * DEMAG_EUNSUPPORTED (the path cannot hold this plan).
@@ -287,8 +297,8 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
  *
  * out (HOST, 10 values): {nx, ny, L, Px, Py, precision, max_batch,
  *                         number of stored layer pairs, stored row length QyS,
- *                         column path: 1 fused, 2 split, 3/4 split-TF32
- *                         variants, 5 fused 512-point}
+ *                         column path: 1 fused, 2 split, 3/4/6/7
+ *                         split-precision variants, 5 fused 512-point}
  * Px, Py are the padded FFT sizes; the stored tensor holds the layer pairs
  * i <= j (the rest follow from reciprocity, t_i N(i<-j)(d) = t_j N(j<-i)(-d)).
  */
@@ -298,7 +308,7 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
  * demag_plan_tensor - copy of the stored Fourier-space tensor.
  *
  * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,
- * layout [kx][pair][component][u] (DEMAG_PREC_SPLIT_TF32 plans:
+ * layout [kx][pair][component][u] (split-precision plans:
  * (Px/2+1) * (Py/2+1) * NB floats, layout [kx][u][component][pair] with
  * each component row npairs rounded up to a multiple of 4 (NB = 6 times
  * that), the padding zero)

@@ -12,7 +12,7 @@ import os
 from . import build as _build
 
 DEMAG_OK, DEMAG_EINVAL, DEMAG_ENOMEM, DEMAG_ECUDA, DEMAG_EUNSUPPORTED = range(5)
-PREC_FP64, PREC_FP32, PREC_SPLIT_TF32 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_SPLIT_TF32, PREC_SPLIT_BF16 = 0, 1, 2, 3
 
 _lib = None
 
@@ -169,7 +169,9 @@ def demag_apply(plan, m, Ms, H, stream=None, info=None):
 def demag_plan_set_path(plan, path):
     """0: the plan's default; 1: fused column kernel, 2: split column kernels;
     split-precision plans: 3 (FP32 cores), 4 (warp-level TF32 MMAs), 6 (tcgen05,
-    their default where it holds the plan).  See demag_plan_set_path in demag.h."""
+    3xTF32), 7 (tcgen05, 3xBF16); 6 or 7 is the default of DEMAG_PREC_SPLIT_TF32
+    or DEMAG_PREC_SPLIT_BF16 plans where it holds the plan.  See
+    demag_plan_set_path in demag.h."""
     _check(lib().demag_plan_set_path(ctypes.c_void_p(plan), int(path)), "demag_plan_set_path")
 
 

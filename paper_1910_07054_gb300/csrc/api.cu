@@ -317,7 +317,7 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
         if (!(std::isfinite(thickness[l]) && thickness[l] > 0))
             return fail(DEMAG_EINVAL, "thickness[" + std::to_string(l) + "] must be finite and > 0");
     if (precision != DEMAG_PREC_FP64 && precision != DEMAG_PREC_FP32 &&
-        precision != DEMAG_PREC_SPLIT_TF32)
+        precision != DEMAG_PREC_SPLIT_TF32 && precision != DEMAG_PREC_SPLIT_BF16)
         return fail(DEMAG_EINVAL, "unknown precision");
     if (max_batch < 1) return fail(DEMAG_EINVAL, "max_batch must be >= 1");
     if ((long long)max_batch * L * 3 > 65535)
@@ -342,7 +342,7 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     p->QyS = tensor_row(p->log2Py, precision == DEMAG_PREC_FP64);
     p->npairs = L * (L + 1) / 2;
     const bool fp64 = precision == DEMAG_PREC_FP64;
-    if (precision == DEMAG_PREC_SPLIT_TF32) {
+    if (precision == DEMAG_PREC_SPLIT_TF32 || precision == DEMAG_PREC_SPLIT_BF16) {
         // split path, dense-product contraction on the tensor cores
         if (!gemm_supported(L, max_batch)) {
             delete p;
@@ -350,8 +350,10 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
         }
         p->split = 1;
         p->umajor = 1;
-        // tcgen05 products where they hold the plan, else the warp-level MMAs
-        p->contract_mode = tc5_supported(L, max_batch, p->npairs) ? 3 : 2;
+        // tcgen05 products where they hold the plan, else the warp-level TF32 MMAs
+        p->contract_mode = tc5_supported(L, max_batch, p->npairs)
+                               ? (precision == DEMAG_PREC_SPLIT_BF16 ? 4 : 3)
+                               : 2;
     } else {
         p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
         p->natural = !p->split && cols512_supported(p->log2Py, L, fp64) ? 1 : 0;
@@ -540,16 +542,17 @@ demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
     const bool fp64 = plan->precision == DEMAG_PREC_FP64;
     if (plan->umajor) {
-        if (path == 0) path = tc5_supported(plan->L, plan->max_batch, plan->npairs) ? 6 : 4;
-        if (path != 3 && path != 4 && path != 6)
-            return fail(DEMAG_EUNSUPPORTED, "split-TF32 plans run path 3, 4 or 6");
-        if (path == 6 && !tc5_supported(plan->L, plan->max_batch, plan->npairs))
-            return fail(DEMAG_EUNSUPPORTED, "path 6 needs an even L <= 64 and max_batch <= 16");
-        plan->contract_mode = path == 4 ? 2 : (path == 6 ? 3 : 1);
+        const bool tc5 = tc5_supported(plan->L, plan->max_batch, plan->npairs);
+        if (path == 0) path = !tc5 ? 4 : (plan->precision == DEMAG_PREC_SPLIT_BF16 ? 7 : 6);
+        if (path != 3 && path != 4 && path != 6 && path != 7)
+            return fail(DEMAG_EUNSUPPORTED, "split-precision plans run path 3, 4, 6 or 7");
+        if ((path == 6 || path == 7) && !tc5)
+            return fail(DEMAG_EUNSUPPORTED, "paths 6 and 7 need an even L <= 64 and max_batch <= 16");
+        plan->contract_mode = path == 3 ? 1 : (path == 4 ? 2 : (path == 6 ? 3 : 4));
         return DEMAG_OK;
     }
-    if (path == 3 || path == 4)
-        return fail(DEMAG_EUNSUPPORTED, "paths 3 and 4 need a DEMAG_PREC_SPLIT_TF32 plan");
+    if (path == 3 || path == 4 || path == 6 || path == 7)
+        return fail(DEMAG_EUNSUPPORTED, "paths 3, 4, 6 and 7 need a split-precision plan");
     if (plan->natural) {
         if (path != 0 && path != 1 && path != 5)
             return fail(DEMAG_EUNSUPPORTED, "plans on the 512-point fused kernel run path 5 only");
@@ -648,7 +651,8 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     out[6] = plan->max_batch;
     out[7] = plan->npairs;
     out[8] = plan->QyS;
-    out[9] = plan->umajor ? (plan->contract_mode == 2 ? 4 : (plan->contract_mode == 3 ? 6 : 3))
+    static const int umajor_path[5] = {3, 3, 4, 6, 7};
+    out[9] = plan->umajor ? umajor_path[plan->contract_mode]
                           : (plan->split ? 2 : (plan->natural ? 5 : 1));
     return DEMAG_OK;
 }

@@ -1,5 +1,7 @@
 // Layer contraction for batches of states on the fifth-generation tensor cores
-// (tcgen05, kind::tf32, accumulators in tensor memory), three TF32 passes.
+// (tcgen05, accumulators in tensor memory), three split passes: TF32 operands
+// (kind::tf32, K = 8 per MMA) or BF16 operands (kind::f16, K = 16 per MMA, half
+// the MMAs for the same K; hi + lo carry 16 significant bits of each value).
 //
 // At one stored frequency entry (kx, u) the contraction of Eq. FFT_v2 for both
 // of its y-frequencies (ky and Py - ky) and all B states is one real product
@@ -55,7 +57,9 @@ constexpr int kTcThreads = 32 * (kTcProd + 6);       // + 4 epilogue, MMA, loade
 constexpr int kTcEpi = kTcProd, kTcMma = kTcProd + 4, kTcPre = kTcProd + 5;  // first warp of each role
 constexpr int kTcN = 64;         // accumulator columns: 2 positions x (re, im) x 16 states
 constexpr int kTcBp = 16;
-constexpr int kTcKC = 16;        // K columns per chunk (two MMA k-steps)
+// K columns per chunk (two MMA k-steps): 16 TF32 or 32 BF16 values, 64 bytes
+// of each S row either way
+template <bool BF> struct TcKC { static constexpr int value = BF ? 32 : 16; };
 constexpr int kTcStages = 3;
 constexpr int kTcCols = 512;     // tensor memory allocated
 constexpr int kTcAcol = 256;     // first column of the A stages
@@ -70,7 +74,7 @@ struct TcShape {
 
 __host__ __device__ inline size_t round128(size_t v) { return (v + 127) / 128 * 128; }
 
-__host__ __device__ inline TcShape tc_shape(int L, int B, int npairs) {
+__host__ __device__ inline TcShape tc_shape(int L, int B, int npairs, int kc = 16) {
     TcShape s;
     s.L = L;
     s.Lp = (L + 7) / 8 * 8;
@@ -78,7 +82,7 @@ __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs) {
     s.planes = B * 3 * L;
     s.R = 3 * s.Lp;
     s.T = (s.R + 127) / 128;
-    s.nch = (s.R + kTcKC - 1) / kTcKC;  // K = R padded to whole chunks (zero columns)
+    s.nch = (s.R + kc - 1) / kc;  // K = R padded to whole chunks (zero columns)
     s.NB = umajor_block(npairs);
     // a state's 3L complex values, padded so that consecutive states start 16
     // bytes apart modulo 128 (the 8 states a warp reads at once hit 8 bank groups)
@@ -86,7 +90,7 @@ __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs) {
     s.raw_bytes = round128((size_t)s.NB * 4);
     s.rows_bytes = round128((size_t)2 * B * s.seg * 8);
     s.in_bytes = s.raw_bytes + s.rows_bytes;  // one input buffer (two of them)
-    s.s_bytes = (size_t)kTcN * kTcKC * 4;
+    s.s_bytes = (size_t)kTcN * 64;  // N rows x 64 bytes of K
     s.stage_bytes = 2 * s.s_bytes;            // S hi, S lo
     s.off_stage = 2 * s.in_bytes;
     s.total = s.off_stage + kTcStages * s.stage_bytes;
@@ -114,30 +118,74 @@ __device__ __forceinline__ void split_tf32(float v, uint32_t &hi, uint32_t &lo) 
     lo = __float_as_uint(v - __uint_as_float(hi));
 }
 
-// One thread: the six MMAs of one 128-row tile and one 16-column chunk of K,
-// A from tensor memory (hi in columns at..at+15, lo in at+16..at+31), S hi and
-// lo from shared memory (descriptors bh, bl; +16 in the start-address field is
-// the second k-step, 256 bytes further):  D (+)= A_lo S_hi + A_hi S_lo + A_hi S_hi
+// Round a finite float to BF16 (8 significant bits), to nearest with ties to
+// even, as the upper 16 bits of a float.
+__device__ __forceinline__ uint32_t bf16_round(uint32_t bits) {
+    return (bits + 0x7FFFu + ((bits >> 16) & 1u)) & 0xFFFF0000u;
+}
+
+// v = hi + lo + r with hi = bf16(v), lo = bf16(v - hi) (|r| <= 2^-18 |v|);
+// returned as the two 16-bit patterns.
+__device__ __forceinline__ void split_bf16(float v, uint32_t &hi, uint32_t &lo) {
+    const uint32_t h = bf16_round(__float_as_uint(v));
+    hi = h >> 16;
+    lo = bf16_round(__float_as_uint(v - __uint_as_float(h))) >> 16;
+}
+
+// Split of one 32-bit operand word: TF32 takes one value per word, BF16 two
+// (the lower K index in the low half).
+template <bool BF> struct Split;
+template <> struct Split<false> {
+    static constexpr int kPerWord = 1;
+    __device__ __forceinline__ static void word(const float *v, uint32_t &hi, uint32_t &lo) {
+        split_tf32(v[0], hi, lo);
+    }
+};
+template <> struct Split<true> {
+    static constexpr int kPerWord = 2;
+    __device__ __forceinline__ static void word(const float *v, uint32_t &hi, uint32_t &lo) {
+        uint32_t h0, l0, h1, l1;
+        split_bf16(v[0], h0, l0);
+        split_bf16(v[1], h1, l1);
+        hi = h0 | (h1 << 16);
+        lo = l0 | (l1 << 16);
+    }
+};
+
+// One thread: the six MMAs of one 128-row tile and one chunk of K (two
+// k-steps), A from tensor memory (hi in columns at..at+15, lo in at+16..at+31;
+// each k-step's 8 columns hold 8 TF32 or 16 BF16 values), S hi and lo from
+// shared memory (descriptors bh, bl; +16 in the start-address field is the
+// second k-step, 256 bytes further):  D (+)= A_lo S_hi + A_hi S_lo + A_hi S_hi
 // for k-steps 0 and 1.  `accumulate` false starts D over.
+#define DEMAG_TC_MMA_CHUNK(KIND)                                                                         \
+    asm volatile(                                                                                        \
+        "{\n\t.reg .pred pa, pt;\n\t"                                                                    \
+        "setp.ne.b32 pa, %9, 0;\n\t"                                                                     \
+        "setp.eq.b32 pt, %9, %9;\n\t"                                                                    \
+        "tcgen05.mma.cta_group::1.kind::" KIND " [%0], [%3], %5, %8, pa;\n\t"                            \
+        "tcgen05.mma.cta_group::1.kind::" KIND " [%0], [%1], %6, %8, pt;\n\t"                            \
+        "tcgen05.mma.cta_group::1.kind::" KIND " [%0], [%1], %5, %8, pt;\n\t"                            \
+        "tcgen05.mma.cta_group::1.kind::" KIND " [%0], [%4], %7, %8, pt;\n\t"                            \
+        "tcgen05.mma.cta_group::1.kind::" KIND " [%0], [%2], %10, %8, pt;\n\t"                           \
+        "tcgen05.mma.cta_group::1.kind::" KIND " [%0], [%2], %7, %8, pt;\n\t}" ::"r"(dt),                \
+        "r"(at), "r"(at + 8), "r"(at + 16), "r"(at + 24), "l"(bh), "l"(bl), "l"(bh + 16), "r"(idesc),   \
+        "r"((unsigned)accumulate), "l"(bl + 16)                                                          \
+        : "memory")
+
+template <bool BF>
 __device__ __forceinline__ void tc_mma_chunk(unsigned dt, unsigned at, uint64_t bh, uint64_t bl, uint32_t idesc,
                                              bool accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred pa, pt;\n\t"
-        "setp.ne.b32 pa, %9, 0;\n\t"
-        "setp.eq.b32 pt, %9, %9;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%3], %5, %8, pa;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %6, %8, pt;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %5, %8, pt;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%4], %7, %8, pt;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %10, %8, pt;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %7, %8, pt;\n\t}" ::"r"(dt),
-        "r"(at), "r"(at + 8), "r"(at + 16), "r"(at + 24), "l"(bh), "l"(bl), "l"(bh + 16), "r"(idesc),
-        "r"((unsigned)accumulate), "l"(bl + 16)
-        : "memory");
+    if (BF)
+        DEMAG_TC_MMA_CHUNK("f16");
+    else
+        DEMAG_TC_MMA_CHUNK("tf32");
 }
+#undef DEMAG_TC_MMA_CHUNK
 
 }  // namespace
 
+template <bool BF>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restrict__ spec2,
                                                                const float *__restrict__ tensor_um,
                                                                const float *__restrict__ ratio, int L, int B,
@@ -149,7 +197,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
     __shared__ __align__(16) float s_tau[64], s_itau[64];
     __shared__ __align__(16) int s_rb[64];  // index of pair (i, i) minus i: pair (i, j >= i) is s_rb[i] + j
     __shared__ int s_abort;
-    const TcShape sh = tc_shape(L, B, npairs);
+    constexpr int KC = TcKC<BF>::value;  // K columns per chunk
+    constexpr int PW = Split<BF>::kPerWord;
+    const TcShape sh = tc_shape(L, B, npairs, KC);
     const int Py = 1 << log2Py, Qy = Py / 2 + 1, Kx = (1 << log2Px) / 2 + 1;
     const int nent = Kx * Qy;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -291,7 +341,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
             slo[ci] = zs * itau_i * (comp >= 4 ? -1.f : 1.f);
         }
         // S unit of this thread: (position pq, state b, core column k4)
-        constexpr int KG = kTcKC / 4;
+        constexpr int KG = 4;  // core matrices (16 bytes of K) per S row and chunk
         const int sv = lane + 32 * sidx;
         const bool sact = !isA && sv < 2 * kTcBp * KG;
         const int k4 = sv & (KG - 1), sb = (sv >> 2) & (kTcBp - 1), spq = (sv >> 6) & 1;
@@ -314,54 +364,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                 if (use >= 1 && !mbar_wait(&st_empty[s], (use - 1) & 1, &g_tc_timeouts)) ok = false;
                 tc_fence_after();
                 if (isA) {
-                    const int kc0 = ch * kTcKC + 8 * h;  // first K column of the block
-                    uint32_t hi[8], lo[8];
-                    if (kc0 < R) {
-                        const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), jb = kc0 - ci * Lp;
-                        const int off = inb + (ci == 0 ? offc[0] : (ci == 1 ? offc[1] : offc[2]));
-                        const float su = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
-                        const float sl = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
-                        const int bu = off + (srb_i + jb) * 4;  // + 4 e: pair (i, jb + e)
-                        const int bl = off + i * 4;             // + 4 s_rb[j]: pair (j, i)
-                        const int4 rb0 = *reinterpret_cast<const int4 *>(s_rb + jb);
-                        const int4 rb1 = *reinterpret_cast<const int4 *>(s_rb + jb + 4);
-                        const float4 tj0 = *reinterpret_cast<const float4 *>(s_tau + jb);
-                        const float4 tj1 = *reinterpret_cast<const float4 *>(s_tau + jb + 4);
-                        const int rbj[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
-                        const float tj[8] = {tj0.x, tj0.y, tj0.z, tj0.w, tj1.x, tj1.y, tj1.z, tj1.w};
-                        const int d = i - jb;  // column e is in the upper triangle iff e >= d
-                        if (jb + 8 <= L) {
+                    // block h of the chunk: K columns KC/2 h .. KC/2 (h + 1) - 1,
+                    // PW sub-blocks of 8 (each within one source component, as
+                    // Lp is a multiple of 8)
+                    float v[8 * PW];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const bool up = e >= d;
-                                const int a = up ? bu + 4 * e : bl + 4 * rbj[e];
-                                const float sc = up ? su : sl * tj[e];
-                                split_tf32(sc * *reinterpret_cast<const float *>(smem + a), hi[e], lo[e]);
+                    for (int sbk = 0; sbk < PW; ++sbk) {
+                        const int kc0 = ch * KC + 8 * PW * h + 8 * sbk;  // first K column of the sub-block
+                        float *vs8 = v + 8 * sbk;
+                        if (kc0 < R) {
+                            const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), jb = kc0 - ci * Lp;
+                            const int off = inb + (ci == 0 ? offc[0] : (ci == 1 ? offc[1] : offc[2]));
+                            const float su = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
+                            const float sl = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
+                            const int bu = off + (srb_i + jb) * 4;  // + 4 e: pair (i, jb + e)
+                            const int bl = off + i * 4;             // + 4 s_rb[j]: pair (j, i)
+                            const int4 rb0 = *reinterpret_cast<const int4 *>(s_rb + jb);
+                            const int4 rb1 = *reinterpret_cast<const int4 *>(s_rb + jb + 4);
+                            const float4 tj0 = *reinterpret_cast<const float4 *>(s_tau + jb);
+                            const float4 tj1 = *reinterpret_cast<const float4 *>(s_tau + jb + 4);
+                            const int rbj[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+                            const float tj[8] = {tj0.x, tj0.y, tj0.z, tj0.w, tj1.x, tj1.y, tj1.z, tj1.w};
+                            const int d = i - jb;  // column e is in the upper triangle iff e >= d
+                            if (jb + 8 <= L) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const bool up = e >= d;
+                                    const int a = up ? bu + 4 * e : bl + 4 * rbj[e];
+                                    const float sc = up ? su : sl * tj[e];
+                                    vs8[e] = sc * *reinterpret_cast<const float *>(smem + a);
+                                }
+                            } else {
+                                // last block of a component: columns j >= L are zero
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const bool in = jb + e < L, up = e >= d;
+                                    const int a = !in ? off : (up ? bu + 4 * e : bl + 4 * rbj[e]);
+                                    const float sc = !in ? 0.f : (up ? su : sl * tj[e]);
+                                    vs8[e] = sc * *reinterpret_cast<const float *>(smem + a);
+                                }
                             }
                         } else {
-                            // last block of a component: columns j >= L are zero
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const bool in = jb + e < L, up = e >= d;
-                                const int a = !in ? off : (up ? bu + 4 * e : bl + 4 * rbj[e]);
-                                const float sc = !in ? 0.f : (up ? su : sl * tj[e]);
-                                split_tf32(sc * *reinterpret_cast<const float *>(smem + a), hi[e], lo[e]);
-                            }
+                            for (int e = 0; e < 8; ++e) vs8[e] = 0.f;
                         }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) hi[e] = lo[e] = 0u;
                     }
+                    uint32_t hi[8], lo[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) Split<BF>::word(v + PW * w, hi[w], lo[w]);
                     const unsigned ta = ta_row + (unsigned)(s * kTcAstage);
                     tc_st8(ta, hi);
                     tc_st8(ta + 16, lo);
                     tc_wait_st();
                 } else if (sact) {
-                    // S unit: one (position, state) and 4 consecutive K columns; the
-                    // 4 complex values give 16 bytes of the core-matrix rows of both
+                    // S unit: one (position, state) and 4 PW consecutive K columns
+                    // (one source component, as Lp is a multiple of 8); the 4 PW
+                    // complex values give 16 bytes of the core-matrix rows of both
                     // its columns of S: rows x, y take (Re, Im), rows z (-Im, Re)
-                    const int kc = ch * kTcKC + 4 * k4;
-                    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+                    constexpr int KU = 4 * PW;
+                    const int kc = ch * KC + KU * k4;
+                    float re[KU], im[KU];
+#pragma unroll
+                    for (int e = 0; e < KU; ++e) re[e] = im[e] = 0.f;
                     if (slive && kc < R) {
                         const int ci = (kc >= Lp) + (kc >= 2 * Lp), jb = kc - ci * Lp;
                         const bool z = ci == 2;
@@ -369,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                         const float sim = z ? 1.f : (ci == 1 ? sy0 : 1.f);
                         const int a = inb + srow + (jb * 3 + ci) * 8;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
+                        for (int e = 0; e < KU; ++e) {
                             if (jb + e < L) {
                                 const float2 mv = *reinterpret_cast<const float2 *>(smem + a + 24 * e);
                                 re[e] = sre * (z ? mv.y : mv.x);
@@ -378,14 +442,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                         }
                     }
                     uint4 hr, lr, hm, lm;
-                    split_tf32(re[0], hr.x, lr.x);
-                    split_tf32(re[1], hr.y, lr.y);
-                    split_tf32(re[2], hr.z, lr.z);
-                    split_tf32(re[3], hr.w, lr.w);
-                    split_tf32(im[0], hm.x, lm.x);
-                    split_tf32(im[1], hm.y, lm.y);
-                    split_tf32(im[2], hm.z, lm.z);
-                    split_tf32(im[3], hm.w, lm.w);
+                    Split<BF>::word(re + 0 * PW, hr.x, lr.x);
+                    Split<BF>::word(re + 1 * PW, hr.y, lr.y);
+                    Split<BF>::word(re + 2 * PW, hr.z, lr.z);
+                    Split<BF>::word(re + 3 * PW, hr.w, lr.w);
+                    Split<BF>::word(im + 0 * PW, hm.x, lm.x);
+                    Split<BF>::word(im + 1 * PW, hm.y, lm.y);
+                    Split<BF>::word(im + 2 * PW, hm.z, lm.z);
+                    Split<BF>::word(im + 3 * PW, hm.w, lm.w);
                     unsigned char *st_hi = smem + sh.off_stage + s * sh.stage_bytes;
                     unsigned char *st_lo = st_hi + sh.s_bytes;
                     *reinterpret_cast<uint4 *>(st_hi + soff_r) = hr;
@@ -404,8 +468,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
     } else if (warp == kTcMma) {
         // MMA issue
         if (lane == 0) {
-            const uint32_t idesc = tc_idesc_tf32(128, kTcN);
-            constexpr unsigned LBO = 128, SBO = (kTcKC / 4) * 128;  // K-adjacent cores; 8-row groups
+            const uint32_t idesc = BF ? tc_idesc_bf16(128, kTcN) : tc_idesc_tf32(128, kTcN);
+            constexpr unsigned LBO = 128, SBO = 4 * 128;  // K-adjacent cores; 8-row groups
             // S descriptors of each stage; one k-step (8 K columns = two core
             // matrices, 256 bytes) further is +16 in the start-address field
             uint64_t dhi[kTcStages], dlo[kTcStages];
@@ -428,7 +492,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                     for (int t = 0; t < sh.T; ++t) {
                         const unsigned dt = tmem + (unsigned)((db * sh.T + t) * kTcN);
                         const unsigned at = tmem + (unsigned)(kTcAcol + s * kTcAstage + 32 * t);
-                        tc_mma_chunk(dt, at, bh, bl, idesc, ch > 0);
+                        tc_mma_chunk<BF>(dt, at, bh, bl, idesc, ch > 0);
                     }
                     tc_commit(&st_empty[s]);
                 }
@@ -504,20 +568,19 @@ bool tc5_supported(int L, int B, int npairs) {
     return tc_shape(L, B, npairs).total + 1024 <= 227 * 1024;  // 1 KB for the static shared memory
 }
 
-cudaError_t launch_contract_tc5(const ApplyArgs &a, cudaStream_t st) {
-    const TcShape sh = tc_shape(a.L, a.B, a.npairs);
+cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st) {
+    const TcShape sh = tc_shape(a.L, a.B, a.npairs, bf16 ? TcKC<true>::value : TcKC<false>::value);
+    auto kernel = bf16 ? k_contract_tc5<true> : k_contract_tc5<false>;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_contract_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.total)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.total)) != cudaSuccess)
         return e;
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int nent = ((1 << a.log2Px) / 2 + 1) * ((1 << a.log2Py) / 2 + 1);
     const int grid = nent < nsm ? nent : nsm;
-    k_contract_tc5<<<grid, kTcThreads, sh.total, st>>>((float2 *)a.spec2, (const float *)a.tensor,
-                                                       (const float *)a.ratio, a.L, a.B, a.log2Px, a.log2Py,
-                                                       a.npairs);
+    kernel<<<grid, kTcThreads, sh.total, st>>>((float2 *)a.spec2, (const float *)a.tensor, (const float *)a.ratio,
+                                               a.L, a.B, a.log2Px, a.log2Py, a.npairs);
     return cudaGetLastError();
 }
 

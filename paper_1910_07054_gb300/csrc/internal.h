@@ -79,9 +79,10 @@ struct ApplyArgs {
     void *spec2 = nullptr;  // split path: [Kx][Py][B][L][3] complex workspace
     int split = 0;        // 1: column transforms and contraction in separate kernels
     int full_pairs = 0;   // 1: tensor holds all L*L pairs (no reciprocity)
-    int contract_mode = 0;  // split path: 0 per-item kernel, 3 dense products on the
-                            // tcgen05 tensor cores (3xTF32, TMEM accumulators), 1 dense products on
-                            // FP32 cores, 2 dense products on tensor cores (3xTF32)
+    int contract_mode = 0;  // split path: 0 per-item kernel, 1 dense products on FP32
+                            // cores, 2 dense products on tensor cores (warp-level 3xTF32), 3 on
+                            // the tcgen05 tensor cores (3xTF32, TMEM accumulators), 4 the same
+                            // with 3xBF16
     int natural = 0;      // 512-point column kernel, tensor in natural folded-ky order
     cudaEvent_t *inner_ev = nullptr;  // split path, optional [4]: before and after its 3 kernels
     const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
@@ -118,7 +119,8 @@ bool rows1024_supported(int log2Px, int nx, bool fp64);
 cudaError_t launch_rows1024(bool inverse, const void *src, void *dst, int nx, int ny, int planes, const void *tw,
                             int log2tw, float out_scale, const void *layer_scale, int L, cudaStream_t st);
 bool tc5_supported(int L, int B, int npairs);
-cudaError_t launch_contract_tc5(const ApplyArgs &a, cudaStream_t st);
+// bf16: three BF16 passes (kind::f16) instead of three TF32 passes.
+cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st);
 // The same count for the tcgen05 contraction kernel.
 cudaError_t read_tc_timeouts(unsigned *dst, cudaStream_t st);
 

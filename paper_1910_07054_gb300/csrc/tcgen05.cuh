@@ -33,6 +33,15 @@ __host__ __device__ constexpr uint32_t tc_idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with BF16 operands and FP32
+// accumulation, both operands K-major: D format F32 (bits 4-5), A and B format
+// BF16 (bits 7-9, 10-12), N / 8 (bits 17-22), M / 16 (bits 24-28).  In tensor
+// memory and in a 16-byte core-matrix row an operand word holds two BF16
+// values, the lower K index in the low half.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Whole warp: allocate `ncols` TMEM columns (power of two, 32..512); the base
 // address is written to *slot (shared memory).
 __device__ __forceinline__ void tc_alloc(unsigned *slot, unsigned ncols) {
