@@ -61,6 +61,8 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the 256x256x8 block, the split-precision variants, the differentiation and "
                         "the surrogate measurements")
+    p.add_argument("--sweep-only", action="store_true",
+                   help="run only the hybrid vs 3D-FFT nz sweep at 256x256 and print its JSON")
     p.add_argument("--mram-only", action="store_true",
                    help="run only the 256x256x8 block (device timing) and print its JSON")
     return p.parse_args()
@@ -530,7 +532,7 @@ def mram_block(args, world, rank, dist, peaks, with_oracle):
     return out
 
 
-def batched_measurement(steps, peaks, n=512, layers=64, paths=(4, 6, 3)):
+def batched_measurement(steps, peaks, n=512, layers=64, paths=(6, 7, 4, 3)):
     """512 x 512 cells (n x n if given), 64 layers, 16 states per apply: the
     split-precision contraction on the tcgen05 tensor cores (path 6, the plan's
     default), with warp-level MMAs (path 4) and the same products on the FP32
@@ -553,7 +555,7 @@ def batched_measurement(steps, peaks, n=512, layers=64, paths=(4, 6, 3)):
                        "states per apply; inputs (%.2f GB)" % (nx, ny, L, B * L * 3 * nx * ny * 4 / 1e9),
            "plan_create_s": build_s}
     fields = {}
-    names = {4: "tensor_cores_3xtf32", 6: "tcgen05_3xtf32", 3: "fp32_cores"}
+    names = {4: "tensor_cores_3xtf32", 6: "tcgen05_3xtf32", 7: "tcgen05_3xbf16", 3: "fp32_cores"}
     for path in paths:
         name = names[path]
         dm.demag_plan_set_path(plan.handle, path)
@@ -570,7 +572,7 @@ def batched_measurement(steps, peaks, n=512, layers=64, paths=(4, 6, 3)):
                                     "rows_inverse": float(st[2])},
                      "contraction_tflops_useful": flops / (st[4] * 1e-3) / 1e12}
     tf32_peak = float(peaks.get("bf16_tflops", 1894.6)) * (1.1 / 2.25)
-    for name in ("tensor_cores_3xtf32", "tcgen05_3xtf32"):
+    for name in ("tensor_cores_3xtf32", "tcgen05_3xtf32", "tcgen05_3xbf16"):
         if name not in out:
             continue
         tc = out[name]
@@ -701,8 +703,9 @@ def run_ours(args):
     if not args.no_extras:
         extras["mram256"] = mram_block(args, world, rank, dist, peaks, with_oracle=not args.no_cpu)
         if world == 1:
-            extras["split_variants"] = batched_measurement(3, peaks, paths=(4, 3))
+            extras["split_variants"] = batched_measurement(3, peaks, paths=(6, 7, 4, 3))
             extras["gradient"] = gradient_measurement(with_oracle=not args.no_parity)
+            extras["nz_sweep"] = nz_sweep()
             extras["surrogate"] = surrogate_measurement()
     if rank == 0:
         c, th, _ = headline_workload()
@@ -790,6 +793,65 @@ def gradient_measurement(steps=20, with_oracle=True):
             "dhz_dt_rel_err": None if ref is None else abs(float(g) - ref) / abs(ref)}
 
 
+def nz_sweep(steps=20, n=256, nzs=(1, 2, 4, 8, 12, 16, 24, 32, 48, 64)):
+    """The scaling sweep of Sec. 3.2 on GB300: n x n cells of 2 x 2 nm, nz layers
+    of 1 nm (one thickness, so that both methods apply), one random state per
+    evaluation, float plans: the hybrid of Eq. FFT_v2 (its default path for the
+    stack) and the equidistant 3D FFT of Eq. FFT_3D.  Device time per
+    evaluation (CUDA events, a 256 MB buffer written before each); fits of
+    t = a nz^2 + b nz + c (hybrid) and t = a nz log2(nz) + b nz + c (3D FFT,
+    the linear term for the nz-proportional FFTs in x and y), and the nz where
+    the 3D FFT becomes the faster."""
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import inputs
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for nz in nzs:
+        m = torch.tensor(inputs.random_unit_vectors((1, nz, n, n), seed=nz), dtype=torch.float32, device="cuda")
+        H = torch.empty_like(m)
+        res = {"nz": nz}
+        for name, make in (("hybrid", lambda: dm.Plan(n, n, 2.0, 2.0, (1.0,) * nz, precision=dm.PREC_FP32)),
+                           ("fft3d", lambda: dm.Plan.equidistant(n, n, nz, 2.0, 2.0, 1.0, precision=dm.PREC_FP32))):
+            t0 = time.perf_counter()
+            plan = make()
+            res[name + "_plan_s"] = time.perf_counter() - t0
+            info = plan.info
+            for k in range(3):
+                flush.fill_(float(k))
+                dm.demag_apply(plan.handle, m, 1.0, H, stream, info)
+            ms = time_steps(lambda: dm.demag_apply(plan.handle, m, 1.0, H, stream, info), steps, stream,
+                            before=lambda k: flush.fill_(float(k)))
+            res[name + "_ms"] = float(np.median(ms))
+            res[name + "_path"] = info["path"]
+            if name == "hybrid":
+                Hh = H.clone()
+            else:
+                res["rel_l2_fft3d_vs_hybrid"] = float(torch.linalg.vector_norm((H - Hh).double()) /
+                                                      torch.linalg.vector_norm(Hh.double()))
+            plan.close()
+        rows.append(res)
+    z = np.array([r["nz"] for r in rows], dtype=float)
+    th = np.array([r["hybrid_ms"] for r in rows])
+    t3 = np.array([r["fft3d_ms"] for r in rows])
+    ch = np.linalg.lstsq(np.stack([z * z, z, np.ones_like(z)], 1), th, rcond=None)[0]
+    c3 = np.linalg.lstsq(np.stack([z * np.log2(np.maximum(z, 1)), z, np.ones_like(z)], 1), t3, rcond=None)[0]
+    grid = np.arange(1, 257)
+    fh = ch[0] * grid ** 2 + ch[1] * grid + ch[2]
+    f3 = c3[0] * grid * np.log2(grid) + c3[1] * grid + c3[2]
+    cross_fit = next((int(g) for g, a, b in zip(grid, fh, f3) if b < a and g >= 2), None)
+    cross_meas = next((r["nz"] for r in rows if r["fft3d_ms"] < r["hybrid_ms"]), None)
+    return {"workload": "%dx%d cells of 2x2 nm, nz layers of 1 nm, 1 random state, float32 plans; device time "
+                        "per evaluation (median of %d, cold L2)" % (n, n, steps),
+            "rows": rows,
+            "fit_hybrid_ms": {"a_nz2": ch[0], "b_nz": ch[1], "c": ch[2]},
+            "fit_fft3d_ms": {"a_nzlog2nz": c3[0], "b_nz": c3[1], "c": c3[2]},
+            "crossover_nz_measured": cross_meas, "crossover_nz_fit": cross_fit}
+
+
 def surrogate_measurement():
     """Sec. 4-like optimisation on the 256 x 256 x 8 stack: 2000 solver samples
     (layer 5 in [0.5, 5] nm, the others +-10%), network training, and Newton on
@@ -830,6 +892,11 @@ def main():
         return
     if args.grad_only:
         print(json.dumps(gradient_measurement(with_oracle=not args.no_parity)), flush=True)
+        return
+    if args.sweep_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(nz_sweep(max(args.steps, 5))), flush=True)
         return
     if args.mram_only:
         import torch

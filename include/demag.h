@@ -151,6 +151,35 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
                                void *stream);
 
 /*
+ * demag_plan_create_equidistant - plan of the equidistant 3D-FFT method.
+ *
+ * Sec. 3.1, Eq. FFT_3D: when all nz layers have one thickness dz, N(i <- j)
+ * depends on i - j alone and the sum over the source layers is a convolution
+ * along z, taken by a third zero-padded FFT of length Pz (the next power of
+ * two >= 2 nz) instead of the explicit per-frequency sum of Eq. FFT_v2.  The
+ * plan holds the tensor of the 2nz - 1 z-offsets transformed in x, y and z:
+ * six real values per (kx, ky, kz) with kx <= Px/2, ky <= Py/2, kz <= Pz/2
+ * (the others follow from the parities of the components), built in double
+ * like demag_plan_create's.  demag_apply, demag_apply_host, demag_apply_timed
+ * and demag_apply_adjoint take the plan unchanged (the same [B][nz][3][ny][nx]
+ * arrays; with equal thicknesses the operator is symmetric); the thickness
+ * derivatives do not (DEMAG_EUNSUPPORTED).  demag_plan_info reports path 8,
+ * the offset count nz in place of the stored pairs and the stored row
+ * length Pz/2 + 1 of kz in place of QyS; demag_plan_tensor copies the tensor,
+ * layout [kx][ky][kz][component] (float or double, components as in
+ * demag_plan_tensor, divided by Px Py Pz).
+ *
+ *   nx, ny, dx, dy   as for demag_plan_create
+ *   nz               number of layers, 1 <= nz <= 256
+ *   dz               the common layer thickness, > 0 and finite
+ *   precision        DEMAG_PREC_FP64 or DEMAG_PREC_FP32 (else
+ *                    DEMAG_EUNSUPPORTED)
+ *   max_batch, stream  as for demag_plan_create
+ */
+demag_status demag_plan_create_equidistant(demag_plan_t *plan, int nx, int ny, int nz, double dx, double dy,
+                                           double dz, int precision, int max_batch, void *stream);
+
+/*
  * demag_apply - demagnetization field of B magnetization states.
  *
  * Eq. FFT_v2 read right to left: forward real-to-complex FFT along x of every

@@ -48,6 +48,8 @@ def lib():
     L.demag_last_error.restype = ctypes.c_char_p
     L.demag_plan_create.argtypes = [ctypes.POINTER(vp), i, i, d, d, dp, i, i, i, vp]
     L.demag_plan_create.restype = i
+    L.demag_plan_create_equidistant.argtypes = [ctypes.POINTER(vp), i, i, i, d, d, d, i, i, vp]
+    L.demag_plan_create_equidistant.restype = i
     L.demag_apply.argtypes = [vp, vp, d, vp, i, vp]
     L.demag_apply.restype = i
     L.demag_apply_timed.argtypes = [vp, vp, d, vp, i, vp, ctypes.POINTER(ctypes.c_float), i]
@@ -126,6 +128,15 @@ def demag_plan_create(nx, ny, dx, dy, thickness, precision=PREC_FP32, max_batch=
     _check(lib().demag_plan_create(ctypes.byref(handle), int(nx), int(ny), float(dx), float(dy), th,
                                    len(thickness), int(precision), int(max_batch), _stream(stream)),
            "demag_plan_create")
+    return handle.value
+
+
+def demag_plan_create_equidistant(nx, ny, nz, dx, dy, dz, precision=PREC_FP32, max_batch=1, stream=None):
+    """Plan of the equidistant 3D-FFT method (nz layers of thickness dz)."""
+    handle = ctypes.c_void_p()
+    _check(lib().demag_plan_create_equidistant(ctypes.byref(handle), int(nx), int(ny), int(nz), float(dx), float(dy),
+                                               float(dz), int(precision), int(max_batch), _stream(stream)),
+           "demag_plan_create_equidistant")
     return handle.value
 
 
@@ -372,6 +383,15 @@ class Plan:
         if H is None:
             H = torch.empty_like(m)
         return demag_apply(self.handle, m, Ms, H, stream, self.info)
+
+    @classmethod
+    def equidistant(cls, nx, ny, nz, dx, dy, dz, precision=PREC_FP32, max_batch=1, stream=None):
+        """Plan of the equidistant 3D-FFT method (Eq. FFT_3D): nz layers of one
+        thickness dz; applied like any plan."""
+        self = cls.__new__(cls)
+        self.handle = demag_plan_create_equidistant(nx, ny, nz, dx, dy, dz, precision, max_batch, stream)
+        self.info = demag_plan_info(self.handle)
+        return self
 
     def close(self):
         if self.handle:

@@ -62,6 +62,7 @@ static void free_plan(demag_plan *p) {
     cudaFree(p->d_dtensor);
     cudaFree(p->d_dH);
     cudaFree(p->d_dot);
+    cudaFree(p->d_twz);
     if (p->h_timeouts) cudaFreeHost(p->h_timeouts);
     delete p;
 }
@@ -132,16 +133,25 @@ static demag_status dalloc(void **ptr, size_t bytes, const char *what) {
     } while (0)
 
 // Builds the plan tensor (layer < 0: pairs i <= j of N) or the derivative
-// tensor d N / d t_layer (all L*L pairs) into dst.
-static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void *dst) {
+// tensor d N / d t_layer (all L*L pairs) into dst; with zoffsets, the
+// 2D-transformed kernels of the pairs (r, 0), r = 0..L-1, in double and
+// natural folded-ky order [Kx][L][6][QyS of double] (equidistant plans).
+static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void *dst, bool zoffsets = false) {
     const int L = p->L;
     std::vector<int> pi, pj;
-    for (int i = 0; i < L; ++i)
-        for (int j = i; j < L; ++j) {
-            pi.push_back(i);
-            pj.push_back(j);
+    if (zoffsets) {
+        for (int r = 0; r < L; ++r) {
+            pi.push_back(r);
+            pj.push_back(0);
         }
-    const int npairs = layer < 0 ? p->npairs : L * L;
+    } else {
+        for (int i = 0; i < L; ++i)
+            for (int j = i; j < L; ++j) {
+                pi.push_back(i);
+                pj.push_back(j);
+            }
+    }
+    const int npairs = zoffsets ? L : (layer < 0 ? p->npairs : L * L);
     std::vector<double> z(L + 1, 0.0);
     for (int l = 0; l < L; ++l) z[l + 1] = z[l] + p->thickness[l];
 
@@ -208,10 +218,11 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
                 rc = cuda_fail(e, "tensor FFT kernels");
                 break;
             }
-            if ((e = launch_extract_tensor(planes, p0, np, npairs, p->log2Px, p->log2Py, p->QyS,
-                                           dst, p->precision == DEMAG_PREC_FP64, st,
-                                           layer < 0 ? p->umajor : 0, p->natural)) !=
-                cudaSuccess) {
+            if ((e = launch_extract_tensor(planes, p0, np, npairs, p->log2Px, p->log2Py,
+                                           zoffsets ? tensor_row(p->log2Py, true) : p->QyS, dst,
+                                           zoffsets || p->precision == DEMAG_PREC_FP64, st,
+                                           zoffsets ? 0 : (layer < 0 ? p->umajor : 0),
+                                           zoffsets ? 1 : p->natural)) != cudaSuccess) {
                 rc = cuda_fail(e, "tensor extraction kernel");
                 break;
             }
@@ -252,6 +263,26 @@ static demag_status ensure_dtensor(demag_plan *p, int layer, cudaStream_t st) {
     DEMAG_TRY(build_tensor(p, st, layer, p->d_dtensor));
     p->dlayer = layer;
     return DEMAG_OK;
+}
+
+// Tensor of an equidistant plan (Eq. FFT_3D): the 2D-transformed kernels of
+// the z-offsets r = 0..L-1 (pairs (r, 0) of the stack), extracted in double and
+// natural folded-ky order, then transformed along z by k_ztensor.
+static demag_status build_tensor3d(demag_plan *p, cudaStream_t st) {
+    const int L = p->L;
+    const int QyS2 = tensor_row(p->log2Py, true);
+    const size_t tmp_bytes = (size_t)p->Kx * L * 6 * QyS2 * sizeof(double);
+    void *tmp = nullptr;
+    DEMAG_TRY(dalloc(&tmp, tmp_bytes, "offset kernel spectra"));
+    demag_status rc = build_tensor(p, st, -1, tmp, true);
+    if (rc == DEMAG_OK) {
+        cudaError_t e = launch_ztensor((const double *)tmp, p->d_tensor, p->precision == DEMAG_PREC_FP64, p->log2Px,
+                                       p->log2Py, QyS2, L, p->log2Pz, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "z-transform of the offset kernels");
+    }
+    cudaFree(tmp);
+    return rc;
 }
 
 }  // namespace demag
@@ -301,9 +332,13 @@ demag_status demag_wait_timeouts(unsigned long long *count) {
     return DEMAG_OK;
 }
 
-demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, double dy,
-                               const double *thickness, int L, int precision, int max_batch,
-                               void *stream) {
+}  // extern "C"
+
+// Plan creation of both methods: 0 the hybrid of Eq. FFT_v2 (any thicknesses),
+// 1 the equidistant 3D FFT of Eq. FFT_3D (all thicknesses equal).
+static demag_status plan_create_impl(demag_plan_t *plan, int nx, int ny, double dx, double dy,
+                                     const double *thickness, int L, int precision, int max_batch,
+                                     void *stream, int method) {
     g_last_error.clear();
     if (!plan) return fail(DEMAG_EINVAL, "plan pointer is NULL");
     if (!thickness) return fail(DEMAG_EINVAL, "thickness pointer is NULL");
@@ -342,7 +377,22 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     p->QyS = tensor_row(p->log2Py, precision == DEMAG_PREC_FP64);
     p->npairs = L * (L + 1) / 2;
     const bool fp64 = precision == DEMAG_PREC_FP64;
-    if (precision == DEMAG_PREC_SPLIT_TF32 || precision == DEMAG_PREC_SPLIT_BF16) {
+    if (method == 1) {
+        if (precision != DEMAG_PREC_FP64 && precision != DEMAG_PREC_FP32) {
+            delete p;
+            return fail(DEMAG_EUNSUPPORTED, "equidistant plans take DEMAG_PREC_FP64 or DEMAG_PREC_FP32");
+        }
+        p->method = 1;
+        p->split = 1;
+        p->contract_mode = 5;
+        p->npairs = L;  // z-offsets r = 0..L-1
+        p->log2Pz = ilog2_ceil(2 * L);
+        if (p->log2Pz < 1) p->log2Pz = 1;
+        if (zconv_smem_bytes(p->log2Pz, fp64) > 220 * 1024) {
+            delete p;
+            return fail(DEMAG_EUNSUPPORTED, "nz above the z-convolution kernel's shared memory");
+        }
+    } else if (precision == DEMAG_PREC_SPLIT_TF32 || precision == DEMAG_PREC_SPLIT_BF16) {
         // split path, dense-product contraction on the tensor cores
         if (!gemm_supported(L, max_batch)) {
             delete p;
@@ -371,8 +421,9 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
     demag_status rc = upload_gauss_legendre();
     const size_t real = fp64 ? sizeof(double) : sizeof(float);
     const size_t cpx = 2 * real;
-    p->tensor_bytes = p->umajor ? (size_t)p->Kx * p->Qy * umajor_block(p->npairs) * real
-                                : (size_t)p->Kx * p->npairs * 6 * p->QyS * real;
+    p->tensor_bytes = p->method == 1 ? (size_t)p->Kx * p->Qy * ((1 << p->log2Pz) / 2 + 1) * 6 * real
+                      : p->umajor    ? (size_t)p->Kx * p->Qy * umajor_block(p->npairs) * real
+                                     : (size_t)p->Kx * p->npairs * 6 * p->QyS * real;
     p->field_bytes_per_state = (size_t)L * 3 * ny * nx * real;
     if (rc == DEMAG_OK) rc = dalloc(&p->d_tensor, p->tensor_bytes, "tensor");
     if (rc == DEMAG_OK && (e = cudaMemset(p->d_tensor, 0, p->tensor_bytes)) != cudaSuccess)
@@ -421,13 +472,44 @@ demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, do
                 rc = cuda_fail(e, "cudaMemcpy(plan constants)");
         }
     }
-    if (rc == DEMAG_OK) rc = build_tensor(p, st, -1, p->d_tensor);
+    if (rc == DEMAG_OK && p->method == 1) {
+        rc = dalloc(&p->d_twz, (size_t)(1 << p->log2Pz) / 2 * cpx, "z twiddles");
+        if (rc == DEMAG_OK) {
+            auto tz64 = twiddles<double2>(p->log2Pz);
+            if (fp64) {
+                e = cudaMemcpy(p->d_twz, tz64.data(), tz64.size() * 16, cudaMemcpyHostToDevice);
+            } else {
+                std::vector<float2> tz32(tz64.size());
+                for (size_t k = 0; k < tz64.size(); ++k) tz32[k] = make_float2((float)tz64[k].x, (float)tz64[k].y);
+                e = cudaMemcpy(p->d_twz, tz32.data(), tz32.size() * 8, cudaMemcpyHostToDevice);
+            }
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpy(z twiddles)");
+        }
+    }
+    if (rc == DEMAG_OK) rc = p->method == 1 ? build_tensor3d(p, st) : build_tensor(p, st, -1, p->d_tensor);
     if (rc != DEMAG_OK) {
         free_plan(p);
         return rc;
     }
     *plan = p;
     return DEMAG_OK;
+}
+
+extern "C" {
+
+demag_status demag_plan_create(demag_plan_t *plan, int nx, int ny, double dx, double dy,
+                               const double *thickness, int L, int precision, int max_batch,
+                               void *stream) {
+    return plan_create_impl(plan, nx, ny, dx, dy, thickness, L, precision, max_batch, stream, 0);
+}
+
+demag_status demag_plan_create_equidistant(demag_plan_t *plan, int nx, int ny, int nz, double dx, double dy,
+                                           double dz, int precision, int max_batch, void *stream) {
+    if (nz < 1) return fail(DEMAG_EINVAL, "nz must be >= 1");
+    if (nz > 256) return fail(DEMAG_EUNSUPPORTED, "nz must be <= 256");
+    if (!(std::isfinite(dz) && dz > 0)) return fail(DEMAG_EINVAL, "dz must be finite and > 0");
+    std::vector<double> th((size_t)nz, dz);
+    return plan_create_impl(plan, nx, ny, dx, dy, th.data(), nz, precision, max_batch, stream, 1);
 }
 
 static demag_status check_apply(demag_plan_t plan, const void *m, double Ms, const void *H, int B) {
@@ -460,6 +542,8 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.split = plan->split;
     a.contract_mode = plan->contract_mode;
     a.natural = plan->natural;
+    a.twz = plan->d_twz;
+    a.log2Pz = plan->log2Pz;
     a.Ms = Ms;
     return a;
 }
@@ -540,6 +624,10 @@ demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, 
 
 demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    if (plan->method == 1) {
+        if (path != 0 && path != 8) return fail(DEMAG_EUNSUPPORTED, "equidistant plans run path 8 only");
+        return DEMAG_OK;
+    }
     const bool fp64 = plan->precision == DEMAG_PREC_FP64;
     if (plan->umajor) {
         const bool tc5 = tc5_supported(plan->L, plan->max_batch, plan->npairs);
@@ -596,6 +684,8 @@ demag_status demag_apply_dthickness(demag_plan_t plan, const void *m, double Ms,
     if (layer < 0 || layer >= plan->L) return fail(DEMAG_EINVAL, "layer out of range");
     if (plan->umajor)
         return fail(DEMAG_EUNSUPPORTED, "thickness derivatives need a DEMAG_PREC_FP64 or DEMAG_PREC_FP32 plan");
+    if (plan->method == 1)
+        return fail(DEMAG_EUNSUPPORTED, "thickness derivatives need a plan of demag_plan_create");
     cudaStream_t st = (cudaStream_t)stream;
     DEMAG_TRY(ensure_dtensor(plan, layer, st));
     ApplyArgs a = apply_args(plan, Ms, B);
@@ -650,9 +740,10 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     out[5] = plan->precision;
     out[6] = plan->max_batch;
     out[7] = plan->npairs;
-    out[8] = plan->QyS;
+    out[8] = plan->method == 1 ? (1 << plan->log2Pz) / 2 + 1 : plan->QyS;
     static const int umajor_path[5] = {3, 3, 4, 6, 7};
-    out[9] = plan->umajor ? umajor_path[plan->contract_mode]
+    out[9] = plan->method == 1 ? 8
+           : plan->umajor      ? umajor_path[plan->contract_mode]
                           : (plan->split ? 2 : (plan->natural ? 5 : 1));
     return DEMAG_OK;
 }

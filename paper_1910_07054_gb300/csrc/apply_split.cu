@@ -291,8 +291,9 @@ static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_
     if (e != cudaSuccess) return e;
     if (iev && (e = cudaEventRecord(iev[1], st)) != cudaSuccess) return e;
     if (a.contract_mode != 0) {
-        e = a.contract_mode >= 3 ? launch_contract_tc5(a, a.contract_mode == 4, st)
-                                 : launch_contract_gemm(a, a.contract_mode == 2, st);
+        e = a.contract_mode == 5   ? launch_zconv(a, sizeof(T) == 8, st)
+            : a.contract_mode >= 3 ? launch_contract_tc5(a, a.contract_mode == 4, st)
+                                   : launch_contract_gemm(a, a.contract_mode == 2, st);
         if (e != cudaSuccess) return e;
         if (iev && (e = cudaEventRecord(iev[2], st)) != cudaSuccess) return e;
         if ((e = columns_inverse()) != cudaSuccess) return e;

@@ -82,11 +82,13 @@ struct ApplyArgs {
     int contract_mode = 0;  // split path: 0 per-item kernel, 1 dense products on FP32
                             // cores, 2 dense products on tensor cores (warp-level 3xTF32), 3 on
                             // the tcgen05 tensor cores (3xTF32, TMEM accumulators), 4 the same
-                            // with 3xBF16
+                            // with 3xBF16, 5 the z-convolution of the equidistant method
     int natural = 0;      // 512-point column kernel, tensor in natural folded-ky order
     cudaEvent_t *inner_ev = nullptr;  // split path, optional [4]: before and after its 3 kernels
     const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
+    const void *twz = nullptr;        // equidistant plans: twiddles for Pz
+    int log2Pz = 0;                   // equidistant plans: padded z size
     double Ms;
 };
 
@@ -124,6 +126,15 @@ cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st);
 // The same count for the tcgen05 contraction kernel.
 cudaError_t read_tc_timeouts(unsigned *dst, cudaStream_t st);
 
+// Equidistant method of Eq. FFT_3D (fft3d.cu): the z-convolution that
+// replaces the layer contraction (contract_mode 5), and the z-transform of the
+// 2D-transformed offset kernels src [Kx][L][6][QyS2] (double, natural folded
+// ky) into the tensor [Kx][Py/2+1][Pz/2+1][6].
+size_t zconv_smem_bytes(int log2Pz, bool fp64);
+cudaError_t launch_zconv(const ApplyArgs &a, bool fp64, cudaStream_t st);
+cudaError_t launch_ztensor(const double *src, void *dst, bool fp64, int log2Px, int log2Py, int QyS2, int L,
+                           int log2Pz, cudaStream_t st);
+
 // Split path (apply_split.cu).
 size_t split_workspace_bytes(int L, int B, int log2Px, int log2Py, bool fp64);
 bool split_supported(int L, int B, bool fp64);
@@ -152,6 +163,9 @@ struct demag_plan {
     int contract_mode = 0;        // split path contraction (see ApplyArgs)
     int umajor = 0;               // tensor layout [Kx][Qy][6][npairs padded] (split-TF32 plans)
     int natural = 0;              // fused 512-point column kernel, natural folded-ky tensor
+    int method = 0;               // 0 hybrid (Eq. FFT_v2), 1 equidistant 3D FFT (Eq. FFT_3D)
+    int log2Pz = 0;               // equidistant plans: padded z size
+    void *d_twz = nullptr;        // equidistant plans: twiddles for Pz
     void *d_tscale = nullptr;     // [2L]: t_l, then 1 / t_l (plan real type)
     void *d_dtensor = nullptr;    // d N / d t_dlayer, all L*L pairs, [Kx][L*L][6][QyS]
     int dlayer = -1;              // layer of d_dtensor (-1: none)

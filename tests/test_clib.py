@@ -65,6 +65,21 @@ def test_other_entry_points_reject_null_and_bad_sizes():
     assert lib.demag_destroy(None) == 0
 
 
+@pytest.mark.parametrize("args,status", [
+    ((4, 4, 0, 2.0, 2.0, 1.0, 1, 1), 1),            # nz < 1
+    ((4, 4, 3, 2.0, 2.0, 0.0, 1, 1), 1),            # dz <= 0
+    ((4, 4, 3, 2.0, 2.0, float("nan"), 1, 1), 1),   # dz not finite
+    ((0, 4, 3, 2.0, 2.0, 1.0, 1, 1), 1),            # nx < 1
+    ((4, 4, 3, 2.0, 2.0, 1.0, 2, 1), 4),            # split precision: not for the 3D method
+    ((4, 4, 300, 2.0, 2.0, 1.0, 1, 1), 4),          # nz above 256
+    ((4, 4, 3, 2.0, 2.0, 1.0, 1, 0), 1),            # max_batch < 1
+])
+def test_equidistant_plan_rejects_bad_arguments(args, status):
+    h = ctypes.c_void_p()
+    assert dm.lib().demag_plan_create_equidistant(ctypes.byref(h), *args, None) == status
+    assert dm.demag_last_error() != ""
+
+
 def test_status_strings():
     names = [dm.demag_status_string(s) for s in range(5)]
     assert names == ["DEMAG_OK", "DEMAG_EINVAL", "DEMAG_ENOMEM", "DEMAG_ECUDA", "DEMAG_EUNSUPPORTED"]
