@@ -473,6 +473,63 @@ demag_status demag_mlp_adam(float *w, void *w_bf16, float *g, float *m1, float *
 demag_status demag_layer_mean(const void *H, int precision, int B, int L, int ny, int nx, int layer,
                               double *out, void *stream);
 
+/*
+ * Micromagnetic relaxation of one layer (Sec. 4: the free layer of the MRAM
+ * cell is relaxed by a limited-memory BFGS energy minimisation at every
+ * applied field of an easy-axis hysteresis loop, the other layers pinned).
+ *
+ * Energy of the relaxed layer (SI units, V the cell volume, fields in tesla):
+ *   exchange    A V sum over in-plane neighbour pairs inside the mask of
+ *               |m_j - m_i|^2 / d^2 (free surfaces at the mask's edge)
+ *   anisotropy  -Ku V sum_i m_z,i^2 (uniaxial, easy axis z)
+ *   Zeeman      -(Js / mu0) V sum_i m_i . b_ext
+ *   demag       -(Js / mu0) V sum_i m_i . (b_self,i / 2 + b_bias,i), b_self the
+ *               field of the layer's own magnetization and b_bias that of the
+ *               other layers, both from demag_apply with Ms = Js / mu0 (one
+ *               saturation magnetization for every magnetic layer).
+ * The unit vectors are parametrized as m = v / |v|; L-BFGS with the given
+ * history and Armijo backtracking; stop when max_i |m_i x b_eff,i| <
+ * tol_torque (tesla), when no step lowers the energy (converged to the
+ * rounding of its sum), or after max_iter iterations.
+ */
+typedef struct {
+    double Js;           /* mu0 Ms (T), > 0 */
+    double A_ex;         /* exchange constant (J/m), >= 0 */
+    double Ku;           /* uniaxial anisotropy along z (J/m^3) */
+    double b_ext[3];     /* applied field mu0 H (T) */
+    double length_unit;  /* metres per length unit of the plan (1e-9 for nm) */
+    double tol_torque;   /* stopping torque (T), > 0 */
+    int max_iter;        /* >= 0 */
+    int history;         /* L-BFGS pairs kept, 1..32 */
+} demag_relax_params;
+
+typedef struct {
+    int iterations;      /* L-BFGS iterations taken */
+    int evaluations;     /* energy and field evaluations (one demag_apply each) */
+    int converged;       /* 1 torque below tolerance, 2 energy at its rounding, 0 max_iter */
+    double energy;       /* energy of the relaxed layer (J) */
+    double max_torque;   /* max_i |m_i x b_eff,i| (T) at the end */
+} demag_relax_stats;
+
+/*
+ * demag_relax_layer - relax layer `layer` of m in place.
+ *
+ *   plan    a DEMAG_PREC_FP64 or DEMAG_PREC_FP32 plan of demag_plan_create
+ *           (max_batch >= 1; one state)
+ *   m       DEVICE, [L][3][ny][nx] of the plan's real type: the other layers
+ *           are read (pinned), layer `layer` is read as the start and
+ *           overwritten by the relaxed unit vectors (zero outside the mask)
+ *   mask    DEVICE, [ny][nx] bytes: nonzero for magnetic cells of the layer
+ *   params  HOST, see demag_relax_params
+ *   stats   HOST, may be NULL
+ * Allocates its workspace (about 2 + 2 history vectors of 3 nx ny doubles and
+ * three stacks) for the call and synchronises `stream`.  Errors: DEMAG_EINVAL
+ * (arguments), DEMAG_EUNSUPPORTED (split-precision or equidistant plan),
+ * DEMAG_ENOMEM, DEMAG_ECUDA.
+ */
+demag_status demag_relax_layer(demag_plan_t plan, void *m, int layer, const unsigned char *mask,
+                               const demag_relax_params *params, demag_relax_stats *stats, void *stream);
+
 /* demag_destroy - free a plan (NULL is accepted).  Synchronises the device. */
 demag_status demag_destroy(demag_plan_t plan);
 

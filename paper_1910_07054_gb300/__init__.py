@@ -8,6 +8,7 @@ from ._lib import (DemagError, Plan, PREC_FP32, PREC_FP64, PREC_SPLIT_BF16, PREC
                    demag_apply_dthickness, demag_apply_host, demag_apply_static, demag_apply_timed,
                    demag_destroy, demag_last_error, demag_layer_mean, demag_mlp_adam,
                    demag_mlp_backward, demag_mlp_forward, demag_mlp_mse, demag_mlp_param_count, demag_plan_create, demag_plan_create_equidistant, demag_plan_info,
+                   demag_relax_layer,
                    demag_plan_set_path, demag_plan_tensor, demag_status_string, demag_tensor_points,
                    demag_tensor_points_dt, demag_thickness_grad, demag_wait_timeouts,
                    demag_selftest_bounded_wait, demag_debug_fail_alloc, lib, library_path)
@@ -18,6 +19,6 @@ __all__ = ["DemagError", "Plan", "PREC_FP32", "PREC_FP64", "PREC_SPLIT_BF16", "P
            "demag_apply_static", "demag_apply_timed", "demag_destroy", "demag_layer_mean",
            "demag_mlp_adam", "demag_mlp_backward", "demag_mlp_forward", "demag_mlp_mse",
            "demag_mlp_param_count", "demag_last_error",
-           "demag_plan_create", "demag_plan_create_equidistant", "demag_plan_info", "demag_plan_tensor", "demag_status_string",
+           "demag_plan_create", "demag_plan_create_equidistant", "demag_plan_info", "demag_relax_layer", "demag_plan_tensor", "demag_status_string",
            "demag_tensor_points", "demag_wait_timeouts", "demag_selftest_bounded_wait",
            "demag_debug_fail_alloc", "lib", "library_path"]

@@ -17,6 +17,19 @@ PREC_FP64, PREC_FP32, PREC_SPLIT_TF32, PREC_SPLIT_BF16 = 0, 1, 2, 3
 _lib = None
 
 
+class RelaxParams(ctypes.Structure):
+    """demag_relax_params of include/demag.h."""
+    _fields_ = [("Js", ctypes.c_double), ("A_ex", ctypes.c_double), ("Ku", ctypes.c_double),
+                ("b_ext", ctypes.c_double * 3), ("length_unit", ctypes.c_double), ("tol_torque", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("history", ctypes.c_int)]
+
+
+class RelaxStats(ctypes.Structure):
+    """demag_relax_stats of include/demag.h."""
+    _fields_ = [("iterations", ctypes.c_int), ("evaluations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("energy", ctypes.c_double), ("max_torque", ctypes.c_double)]
+
+
 class DemagError(RuntimeError):
     def __init__(self, status, where, detail):
         self.status = status
@@ -87,6 +100,8 @@ def lib():
     L.demag_mlp_adam.restype = i
     L.demag_layer_mean.argtypes = [vp, i, i, i, i, i, i, vp, vp]
     L.demag_layer_mean.restype = i
+    L.demag_relax_layer.argtypes = [vp, vp, i, vp, ctypes.POINTER(RelaxParams), ctypes.POINTER(RelaxStats), vp]
+    L.demag_relax_layer.restype = i
     L.demag_destroy.argtypes = [vp]
     L.demag_destroy.restype = i
     L.demag_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
@@ -359,6 +374,29 @@ def demag_selftest_bounded_wait(limit_cycles, stream=None):
 def demag_debug_fail_alloc(after):
     """Refuse the library's device allocation after the next `after` ones (host-side injection)."""
     _check(lib().demag_debug_fail_alloc(int(after)), "demag_debug_fail_alloc")
+
+
+def demag_relax_layer(plan, m, layer, mask, Js, A_ex, Ku, b_ext, length_unit=1e-9, tol_torque=1e-5,
+                      max_iter=2000, history=10, stream=None, info=None):
+    """Relax layer `layer` of m ([L, 3, ny, nx] or [1, L, 3, ny, nx], CUDA, the plan's
+    dtype) in place: L-BFGS minimisation of exchange + uniaxial anisotropy (z) +
+    Zeeman + demag energy, the other layers pinned.  mask: CUDA uint8 [ny, nx].
+    Returns the stats as a dict."""
+    import torch
+    info = info or demag_plan_info(plan)
+    if _field_check(m, info, "m") != 1:
+        raise ValueError("m must hold one state")
+    if mask.dtype != torch.uint8 or not mask.is_cuda or tuple(mask.shape) != (info["ny"], info["nx"]) \
+            or not mask.is_contiguous():
+        raise ValueError("mask must be a contiguous CUDA uint8 tensor [ny, nx]")
+    prm = RelaxParams(float(Js), float(A_ex), float(Ku), (ctypes.c_double * 3)(*[float(b) for b in b_ext]),
+                      float(length_unit), float(tol_torque), int(max_iter), int(history))
+    st = RelaxStats()
+    _check(lib().demag_relax_layer(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), int(layer),
+                                   ctypes.c_void_p(mask.data_ptr()), ctypes.byref(prm), ctypes.byref(st),
+                                   _stream(stream)), "demag_relax_layer")
+    return {"iterations": st.iterations, "evaluations": st.evaluations, "converged": st.converged,
+            "energy": st.energy, "max_torque": st.max_torque}
 
 
 def demag_destroy(plan):
