@@ -56,6 +56,10 @@ def parse_args():
                    help="in-plane cells per side of the batched measurement (smaller for profiling)")
     p.add_argument("--batched-layers", type=int, default=64,
                    help="layers of the batched measurement (the first of its 64; fewer for profiling)")
+    p.add_argument("--batched-paths", default="6,7,4,3",
+                   help="contraction paths of the batched measurement (comma separated)")
+    p.add_argument("--hysteresis-only", action="store_true",
+                   help="run only the Sec. 4 MRAM free-layer hysteresis and print its JSON")
     p.add_argument("--grad-only", action="store_true",
                    help="run only the differentiation measurement and print its JSON")
     p.add_argument("--no-extras", action="store_true",
@@ -280,8 +284,8 @@ def headline_workload():
     th = [float(t) for t in inputs.thicknesses(HEADLINE)]
     desc = ("layer scaling + batch: %dx%d cells of %gx%g nm, %d layers with thicknesses uniform in [%g, %g] nm "
             "(seed %d), %d random unit-vector states per apply (normalised N(0,1) triples); Ms = %g A/m; float32 "
-            "FFTs, split-precision contraction (3xTF32, float accumulate) on the tcgen05 tensor cores, float64 "
-            "tensor set-up"
+            "FFTs, split-precision contraction (3xBF16 passes, float accumulate) on the tcgen05 tensor cores, "
+            "float64 tensor set-up"
             % (c["nx"], c["ny"], c["dx"], c["dy"], len(th), c["thickness_range"][0], c["thickness_range"][1],
                c["seed"], c["batch"], inputs.MS_DEFAULT))
     return c, th, desc
@@ -418,7 +422,8 @@ def split_stage_names(info):
     r = "1024" if info["Px"] == 1024 else ""
     cfwd = "k_columns_forward1024" if info["Py"] == 1024 else "k_columns_forward"
     cinv = "k_columns_inverse1024" if info["Py"] == 1024 else "k_columns_inverse"
-    contract = {6: "k_contract_tc5", 4: "k_contract_tc", 3: "k_contract_gemm"}.get(info["path"], "k_contract")
+    contract = {6: "k_contract_tc5<false>", 7: "k_contract_tc5<true>", 4: "k_contract_tc",
+                3: "k_contract_gemm"}.get(info["path"], "k_contract")
     return ["k_rows_forward" + r, cfwd, contract, cinv, "k_rows_inverse" + r]
 
 
@@ -608,7 +613,7 @@ def headline_measurement(args, world, rank, dist, peaks):
     m_np = inputs.random_unit_vectors((B, L, ny, nx), seed=rank_seed(rank))
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    plan = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_BF16, max_batch=B)
     plan_s = time.perf_counter() - t0
     info = plan.info
     m = torch.tensor(m_np, dtype=torch.float32, device="cuda")
@@ -654,7 +659,7 @@ def headline_measurement(args, world, rank, dist, peaks):
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": T, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 FFTs, 3xTF32 contraction with f32 accumulate", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 FFTs, 3xBF16 contraction with f32 accumulate", "data": "synthetic",
         "config": headline_config(c, th, desc, world, info),
         "gcell_layers_per_s": nx * ny * L * value / 1e9,
         "hbm_frac_min_bytes": ((2 * field + tensor) / (T * 1e-3) / 1e9) / peak,
@@ -706,6 +711,7 @@ def run_ours(args):
             extras["split_variants"] = batched_measurement(3, peaks, paths=(6, 7, 4, 3))
             extras["gradient"] = gradient_measurement(with_oracle=not args.no_parity)
             extras["nz_sweep"] = nz_sweep()
+            extras["hysteresis"] = hysteresis_measurement()
             extras["surrogate"] = surrogate_measurement()
     if rank == 0:
         c, th, _ = headline_workload()
@@ -852,6 +858,35 @@ def nz_sweep(steps=20, n=256, nzs=(1, 2, 4, 8, 12, 16, 24, 32, 48, 64)):
             "crossover_nz_measured": cross_meas, "crossover_nz_fit": cross_fit}
 
 
+def hysteresis_measurement(steps=2000, b_max=2.5):
+    """Sec. 4 switching simulation: the MRAM stack (64 x 64 cells over the 60 nm
+    disk, layers [5, 1, 3.44, 1, 3] nm, the SAFM layers pinned +z / -z), CoFe free
+    layer (Js = 1.75 T, A = 1.5e-11 J/m, Ku = 2.09e6 J/m^3 along z) relaxed by
+    L-BFGS at each of `steps` field values from +b_max to -b_max along z (float
+    plan); the sweep stops a few steps after the free layer switched."""
+    import numpy as np
+    import torch
+
+    import paper_1910_07054_gb300 as dm
+    from paper_1910_07054_gb300 import micromag as pmm
+    dx, th, m, mask, layer = pmm.mram_stack()
+    plan = dm.Plan(64, 64, dx, dx, th, precision=dm.PREC_FP32)
+    mt = torch.tensor(m, dtype=torch.float32, device="cuda")
+    bs = pmm.field_steps(b_max, steps)
+    t0 = time.perf_counter()
+    loop = pmm.hysteresis(plan, mt, layer, mask, bs, tol_torque=1e-4, stop_after_switch=5)
+    wall = time.perf_counter() - t0
+    plan.close()
+    b_sw = pmm.switching_field(loop)
+    return {"workload": "Sec. 4 MRAM stack 64x64 cells over 60 nm, layers [5, 1, 3.44, 1, 3] nm, SAFM pinned, CoFe free "
+                        "layer; %d field steps from +%g to -%g T along z (%.2f mT), L-BFGS relaxation (torque < 1e-4 T) "
+                        "at each" % (steps, b_max, b_max, 2e3 * b_max / steps),
+            "switching_field_T": b_sw, "paper_switching_field_T": 1.51,
+            "field_steps_run": len(loop), "relaxation_iterations": int(sum(x[2] for x in loop)),
+            "wall_s": wall, "mz_at_zero_field": float(np.interp(0.0, [x[0] for x in loop][::-1],
+                                                                [x[1] for x in loop][::-1]))}
+
+
 def surrogate_measurement():
     """Sec. 4-like optimisation on the 256 x 256 x 8 stack: 2000 solver samples
     (layer 5 in [0.5, 5] nm, the others +-10%), network training, and Newton on
@@ -887,11 +922,17 @@ def surrogate_measurement():
 def main():
     args = parse_args()
     if args.batched_only:
-        print(json.dumps(batched_measurement(max(args.steps, 1), load_peaks(), args.batched_n, args.batched_layers)),
-              flush=True)
+        paths = tuple(int(x) for x in args.batched_paths.split(","))
+        print(json.dumps(batched_measurement(max(args.steps, 1), load_peaks(), args.batched_n, args.batched_layers,
+                                             paths)), flush=True)
         return
     if args.grad_only:
         print(json.dumps(gradient_measurement(with_oracle=not args.no_parity)), flush=True)
+        return
+    if args.hysteresis_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(hysteresis_measurement()), flush=True)
         return
     if args.sweep_only:
         import torch
