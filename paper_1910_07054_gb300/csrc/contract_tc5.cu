@@ -42,6 +42,8 @@
 // that the warps with two A blocks are in the upper lane quarters, away from
 // the MMA warp's scheduler.  Lanes that hold no row hold whatever tensor memory
 // held; they only feed accumulator rows that are never read.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "internal.h"
@@ -143,12 +145,16 @@ template <> struct Split<false> {
 };
 template <> struct Split<true> {
     static constexpr int kPerWord = 2;
+    // the same rounding as split_bf16, two values at a time with the
+    // hardware's paired conversion (round to nearest even): six instructions
+    // for the pair
     __device__ __forceinline__ static void word(const float *v, uint32_t &hi, uint32_t &lo) {
-        uint32_t h0, l0, h1, l1;
-        split_bf16(v[0], h0, l0);
-        split_bf16(v[1], h1, l1);
-        hi = h0 | (h1 << 16);
-        lo = l0 | (l1 << 16);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);  // .x (low half) = v[0]
+        const uint32_t hb = *reinterpret_cast<const uint32_t *>(&h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v[0] - __uint_as_float(hb << 16),
+                                                       v[1] - __uint_as_float(hb & 0xFFFF0000u));
+        hi = hb;
+        lo = *reinterpret_cast<const uint32_t *>(&l);
     }
 };
 
