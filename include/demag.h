@@ -287,12 +287,15 @@ demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *
 /*
  * demag_apply_host - demag_apply on HOST buffers (end-to-end call).
  *
- * With pinned (page-locked, device-mapped) m and H, the kernels read m from
- * and write H to host memory directly over the host link, which overlaps the
- * transfers with the row transforms; other host memory is copied through the
- * plan's device staging buffers (allocated on first use) before and after
- * demag_apply.  Either way the call synchronises the stream before it
- * returns and the field is identical.  Returns DEMAG_ECUDA (message in
+ * With pinned (page-locked) m and H and B >= 2, the batch is copied through
+ * the plan's device staging buffers (allocated on first use) in up to four
+ * chunks of whole states on a copy stream of the plan, each chunk's input copy
+ * overlapping the row transforms of the chunk before it and each output copy
+ * the inverse row transforms of the chunk after it.  With one state in
+ * pinned, device-mapped buffers the kernels read m from and write H to host
+ * memory directly over the host link.  Other host memory is copied through
+ * the staging buffers before and after demag_apply.  Every way the call
+ * synchronises the stream before it returns and the field is identical.  Returns DEMAG_ECUDA (message in
  * demag_last_error) if a bounded device wait on this device gave up since the
  * timeouts were last reported (see demag_wait_timeouts): the field is then
  * invalid.
@@ -302,6 +305,30 @@ demag_status demag_thickness_grad(demag_plan_t plan, const void *m, const void *
  */
 demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, void *H_host,
                               int B, void *stream);
+
+/*
+ * demag_apply_host_async - demag_apply_host for a stream of batches.
+ *
+ * The pipelined path of demag_apply_host (page-locked m and H only, else
+ * DEMAG_EINVAL), without the synchronisation: the call alternates between two
+ * staging sets of the plan (the second allocated on first use) and returns once
+ * the copies and kernels are enqueued, so that consecutive calls overlap one
+ * batch's input copies and the previous batch's output copies with the
+ * kernels.  m_host must stay unchanged and H_host unread until
+ * demag_apply_host_wait returns; at most two calls may be outstanding per set
+ * of host buffers the caller alternates (a call reuses the staging set of the
+ * call two before).  Bounded-wait timeouts are reported by
+ * demag_apply_host_wait.
+ */
+demag_status demag_apply_host_async(demag_plan_t plan, const void *m_host, double Ms, void *H_host,
+                                    int B, void *stream);
+
+/*
+ * demag_apply_host_wait - wait for every demag_apply_host_async call on the
+ * plan (its copy stream) and for `stream`; DEMAG_ECUDA if a bounded device wait
+ * gave up meanwhile (see demag_wait_timeouts).
+ */
+demag_status demag_apply_host_wait(demag_plan_t plan, void *stream);
 
 /*
  * demag_apply_timed - demag_apply with per-kernel device timing.

@@ -5,7 +5,8 @@ The compute path is ``libdemag.so`` (CUDA kernels behind the C ABI of
 (``_lib``) and the seeded input generators (``inputs``).
 """
 from ._lib import (DemagError, Plan, PREC_FP32, PREC_FP64, PREC_SPLIT_BF16, PREC_SPLIT_TF32, demag_apply, demag_apply_adjoint,
-                   demag_apply_dthickness, demag_apply_host, demag_apply_static, demag_apply_timed,
+                   demag_apply_dthickness, demag_apply_host, demag_apply_host_async, demag_apply_host_wait,
+                   demag_apply_static, demag_apply_timed,
                    demag_destroy, demag_last_error, demag_layer_mean, demag_mlp_adam,
                    demag_mlp_backward, demag_mlp_forward, demag_mlp_mse, demag_mlp_param_count, demag_plan_create, demag_plan_create_equidistant, demag_plan_info,
                    demag_relax_layer,
@@ -15,7 +16,7 @@ from ._lib import (DemagError, Plan, PREC_FP32, PREC_FP64, PREC_SPLIT_BF16, PREC
 
 __all__ = ["DemagError", "Plan", "PREC_FP32", "PREC_FP64", "PREC_SPLIT_BF16", "PREC_SPLIT_TF32", "demag_apply", "demag_apply_adjoint",
            "demag_apply_dthickness", "demag_plan_set_path", "demag_tensor_points_dt",
-           "demag_thickness_grad", "demag_apply_host",
+           "demag_thickness_grad", "demag_apply_host", "demag_apply_host_async", "demag_apply_host_wait",
            "demag_apply_static", "demag_apply_timed", "demag_destroy", "demag_layer_mean",
            "demag_mlp_adam", "demag_mlp_backward", "demag_mlp_forward", "demag_mlp_mse",
            "demag_mlp_param_count", "demag_last_error",

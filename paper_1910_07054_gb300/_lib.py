@@ -69,6 +69,10 @@ def lib():
     L.demag_apply_timed.restype = i
     L.demag_apply_host.argtypes = [vp, vp, d, vp, i, vp]
     L.demag_apply_host.restype = i
+    L.demag_apply_host_async.argtypes = [vp, vp, d, vp, i, vp]
+    L.demag_apply_host_async.restype = i
+    L.demag_apply_host_wait.argtypes = [vp, vp]
+    L.demag_apply_host_wait.restype = i
     L.demag_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.demag_plan_info.restype = i
     L.demag_plan_tensor.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -276,6 +280,24 @@ def demag_apply_host(plan, m, Ms, H, stream=None, info=None):
                                   ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)),
            "demag_apply_host")
     return H
+
+
+def demag_apply_host_async(plan, m, Ms, H, stream=None, info=None):
+    """Enqueue demag_apply_host on page-locked host tensors without waiting;
+    H is valid after demag_apply_host_wait."""
+    info = info or demag_plan_info(plan)
+    B = _field_check(m, info, "m", device=False)
+    if _field_check(H, info, "H", device=False) != B or H.shape != m.shape:
+        raise ValueError("H must have the shape of m")
+    _check(lib().demag_apply_host_async(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), float(Ms),
+                                        ctypes.c_void_p(H.data_ptr()), int(B), _stream(stream)),
+           "demag_apply_host_async")
+    return H
+
+
+def demag_apply_host_wait(plan, stream=None):
+    """Wait for every demag_apply_host_async of the plan."""
+    _check(lib().demag_apply_host_wait(ctypes.c_void_p(plan), _stream(stream)), "demag_apply_host_wait")
 
 
 def demag_plan_tensor(plan, out, stream=None):

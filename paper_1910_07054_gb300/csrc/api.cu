@@ -57,6 +57,8 @@ static void free_plan(demag_plan *p) {
     cudaFree(p->d_spec);
     cudaFree(p->d_stage_m);
     cudaFree(p->d_stage_H);
+    cudaFree(p->d_stage2_m);
+    cudaFree(p->d_stage2_H);
     cudaFree(p->d_spec2);
     cudaFree(p->d_tscale);
     cudaFree(p->d_dtensor);
@@ -64,6 +66,11 @@ static void free_plan(demag_plan *p) {
     cudaFree(p->d_dot);
     cudaFree(p->d_twz);
     if (p->h_timeouts) cudaFreeHost(p->h_timeouts);
+    for (auto &set : p->pipe_ev)
+        for (cudaEvent_t ev : set)
+            if (ev) cudaEventDestroy(ev);
+    if (p->copy_st) cudaStreamDestroy(p->copy_st);
+    if (p->copy_st2) cudaStreamDestroy(p->copy_st2);
     delete p;
 }
 
@@ -586,20 +593,123 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
     return timeout_status(plan, "demag_apply_timed");
 }
 
+// demag_apply_host for page-locked buffers and a batch of states: the batch is
+// cut into up to four chunks of whole states; chunk c's input copy (on the
+// plan's input copy stream) overlaps the row transforms of chunk c - 1, the
+// columns and layer sum run on the whole batch, and chunk c's output copy (on
+// the output copy stream) overlaps the inverse row transforms of chunk c + 1.  With async the call alternates
+// between two staging sets and returns without waiting: the next call's input
+// copies then overlap this call's columns and layer sum, and this call's output
+// copies the next call's work.
+static demag_status apply_host_pipelined(demag_plan_t plan, const void *m_host, double Ms, void *H_host, int B,
+                                         cudaStream_t st, bool async) {
+    const size_t full = plan->field_bytes_per_state * (size_t)plan->max_batch;
+    int set = 0;
+    if (async) set = plan->stage_set ^= 1;
+    void *&stm = set ? plan->d_stage2_m : plan->d_stage_m;
+    void *&sth = set ? plan->d_stage2_H : plan->d_stage_H;
+    if (!stm) DEMAG_TRY(dalloc(&stm, full, "host staging"));
+    if (!sth) DEMAG_TRY(dalloc(&sth, full, "host staging"));
+    if (!plan->copy_st) DEMAG_CUDA(cudaStreamCreateWithFlags(&plan->copy_st, cudaStreamNonBlocking));
+    if (!plan->copy_st2) DEMAG_CUDA(cudaStreamCreateWithFlags(&plan->copy_st2, cudaStreamNonBlocking));
+    for (cudaEvent_t &ev : plan->pipe_ev[set])
+        if (!ev) DEMAG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    const bool fp64 = plan->precision == DEMAG_PREC_FP64;
+    const size_t per_state = plan->field_bytes_per_state;
+    const size_t spec_state = (size_t)plan->L * 3 * plan->Kx * plan->ny * (fp64 ? 16 : 8);
+    const int nch = B < 4 ? B : 4;
+    int b0s[5];
+    for (int c = 0; c <= nch; ++c) b0s[c] = (int)((long long)B * c / nch);
+    cudaStream_t cs = plan->copy_st, cs2 = plan->copy_st2;  // input, output copies
+    cudaEvent_t *ev = plan->pipe_ev[set];
+    const char *mh = (const char *)m_host;
+    char *hh = (char *)H_host, *sm = (char *)stm, *sh = (char *)sth;
+    if (!async) {
+        // the staging buffers are free once earlier work on st is done
+        DEMAG_CUDA(cudaEventRecord(ev[0], st));
+        DEMAG_CUDA(cudaStreamWaitEvent(cs, ev[0], 0));
+    } else {
+        // this set's input buffer is free once its previous row transforms read it
+        DEMAG_CUDA(cudaStreamWaitEvent(cs, ev[9], 0));
+    }
+    for (int c = 0; c < nch; ++c) {
+        const size_t off = (size_t)b0s[c] * per_state, n = (size_t)(b0s[c + 1] - b0s[c]) * per_state;
+        DEMAG_CUDA(cudaMemcpyAsync(sm + off, mh + off, n, cudaMemcpyHostToDevice, cs));
+        DEMAG_CUDA(cudaEventRecord(ev[1 + c], cs));
+    }
+    const ApplyArgs a = apply_args(plan, Ms, B);
+    auto chunk = [&](int c) {
+        ApplyArgs ac = a;
+        ac.B = b0s[c + 1] - b0s[c];
+        ac.spec = (char *)a.spec + (size_t)b0s[c] * spec_state;
+        return ac;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+        if ((e = cudaStreamWaitEvent(st, ev[1 + c], 0)) == cudaSuccess)
+            e = launch_apply_stage(chunk(c), 0, sm + (size_t)b0s[c] * per_state, nullptr, fp64, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[9], st);
+    if (e == cudaSuccess) e = launch_apply_stage(a, 1, nullptr, nullptr, fp64, st);
+    // this set's output buffer is free once its previous output copies are done
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[10], 0);
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+        const size_t off = (size_t)b0s[c] * per_state, n = (size_t)(b0s[c + 1] - b0s[c]) * per_state;
+        if ((e = launch_apply_stage(chunk(c), 2, nullptr, sh + off, fp64, st)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(ev[5 + c], st)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(cs2, ev[5 + c], 0)) != cudaSuccess) break;
+        e = cudaMemcpyAsync(hh + off, sh + off, n, cudaMemcpyDeviceToHost, cs2);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[10], cs2);
+    if (e == cudaSuccess && !async) e = cudaStreamWaitEvent(st, ev[10], 0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(cs2);
+        return cuda_fail(e, "demag_apply_host pipelined batch");
+    }
+    if (async) return DEMAG_OK;
+    DEMAG_CUDA(enqueue_timeout_read(plan, st));
+    DEMAG_CUDA(cudaStreamSynchronize(st));
+    return timeout_status(plan, "demag_apply_host");
+}
+
+demag_status demag_apply_host_async(demag_plan_t plan, const void *m_host, double Ms, void *H_host, int B,
+                                    void *stream) {
+    demag_status rc = check_apply(plan, m_host, Ms, H_host, B);
+    if (rc != DEMAG_OK) return rc;
+    cudaPointerAttributes am, ah;
+    const bool pinned = cudaPointerGetAttributes(&am, m_host) == cudaSuccess && am.type == cudaMemoryTypeHost &&
+                        cudaPointerGetAttributes(&ah, H_host) == cudaSuccess && ah.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    if (!pinned) return fail(DEMAG_EINVAL, "demag_apply_host_async needs page-locked m and H");
+    return apply_host_pipelined(plan, m_host, Ms, H_host, B, (cudaStream_t)stream, true);
+}
+
+demag_status demag_apply_host_wait(demag_plan_t plan, void *stream) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->copy_st) DEMAG_CUDA(cudaStreamSynchronize(plan->copy_st));
+    if (plan->copy_st2) DEMAG_CUDA(cudaStreamSynchronize(plan->copy_st2));
+    DEMAG_CUDA(enqueue_timeout_read(plan, st));
+    DEMAG_CUDA(cudaStreamSynchronize(st));
+    return timeout_status(plan, "demag_apply_host_wait");
+}
+
 demag_status demag_apply_host(demag_plan_t plan, const void *m_host, double Ms, void *H_host, int B,
                               void *stream) {
     demag_status rc = check_apply(plan, m_host, Ms, H_host, B);
     if (rc != DEMAG_OK) return rc;
     const size_t bytes = plan->field_bytes_per_state * (size_t)B;
     cudaStream_t st = (cudaStream_t)stream;
-    // pinned (page-locked, device-mapped) buffers: the kernels read m and write
-    // H in host memory directly, so the transfers overlap the row transforms
     cudaPointerAttributes am, ah;
-    const bool direct = cudaPointerGetAttributes(&am, m_host) == cudaSuccess && am.type == cudaMemoryTypeHost &&
-                        am.devicePointer && cudaPointerGetAttributes(&ah, H_host) == cudaSuccess &&
-                        ah.type == cudaMemoryTypeHost && ah.devicePointer;
+    const bool pinned = cudaPointerGetAttributes(&am, m_host) == cudaSuccess && am.type == cudaMemoryTypeHost &&
+                        cudaPointerGetAttributes(&ah, H_host) == cudaSuccess && ah.type == cudaMemoryTypeHost;
     cudaGetLastError();  // attribute queries of unregistered memory may leave an error
-    if (direct) {
+    // a batch in page-locked buffers: copies pipelined with the row transforms
+    if (pinned && B >= 2) return apply_host_pipelined(plan, m_host, Ms, H_host, B, st, false);
+    // one state in pinned (device-mapped) buffers: the kernels read m and write
+    // H in host memory directly, so the transfers overlap the row transforms
+    if (pinned && am.devicePointer && ah.devicePointer) {
         cudaError_t e = launch_apply(apply_args(plan, Ms, B), am.devicePointer, ah.devicePointer,
                                      plan->precision == DEMAG_PREC_FP64, st);
         if (e != cudaSuccess) return cuda_fail(e, "demag_apply_host kernels");

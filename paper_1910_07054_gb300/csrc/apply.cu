@@ -320,9 +320,10 @@ static cudaError_t launch_fused(const ApplyArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Row transforms of the a.B states of a (forward: m -> a.spec; inverse:
+// a.spec -> H, cropped and scaled by -Ms).
 template <typename T>
-static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t st,
-                              cudaEvent_t *ev) {
+static cudaError_t rows_stage(const ApplyArgs &a, const T *m, T *H, bool forward, cudaStream_t st) {
     using C = typename cpx_of<T>::type;
     const int Px = 1 << a.log2Px;
     const int planes = a.B * a.L * 3;
@@ -330,47 +331,53 @@ static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t
     const int chunks = (a.ny + 2 * npair - 1) / (2 * npair);
     const size_t smem_rows = (size_t)npair * (Px + 1) * sizeof(C);
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_rows_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_rows);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rows_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_rows);
-    if (e != cudaSuccess) return e;
+    if (a.log2Px == 9) return launch_rows512<T>(a, m, H, forward, st);
+    if (rows1024_supported(a.log2Px, a.nx, sizeof(T) == 8))
+        return forward ? launch_rows1024(false, m, a.spec, a.nx, a.ny, planes, a.twx, a.log2twx, 0.f, a.in_scale,
+                                         a.L, st)
+                       : launch_rows1024(true, a.spec, H, a.nx, a.ny, planes, a.twx, a.log2twx, (float)(-a.Ms),
+                                         a.out_scale, a.L, st);
     dim3 grid_rows(chunks, planes);
-    const bool rows512 = a.log2Px == 9;
-    const bool rows1024 = rows1024_supported(a.log2Px, a.nx, sizeof(T) == 8);
-    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if (rows512)
-        e = launch_rows512<T>(a, m, H, true, st);
-    else if (rows1024)
-        e = launch_rows1024(false, m, a.spec, a.nx, a.ny, planes, a.twx, a.log2twx, 0.f, a.in_scale, a.L, st);
-    else {
-        k_rows_forward<T><<<grid_rows, kRowThreads, smem_rows, st>>>(m, (C *)a.spec, a.nx, a.ny, a.log2Px,
-                                                                     npair, (const C *)a.twx, a.log2twx,
+    if (forward) {
+        e = cudaFuncSetAttribute(k_rows_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows);
+        if (e != cudaSuccess) return e;
+        k_rows_forward<T><<<grid_rows, kRowThreads, smem_rows, st>>>(m, (C *)a.spec, a.nx, a.ny, a.log2Px, npair,
+                                                                     (const C *)a.twx, a.log2twx,
                                                                      (const T *)a.in_scale, a.L);
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return e;
-    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    e = a.split ? launch_split_columns(a, sizeof(T) == 8, st)
-                : (a.natural ? launch_cols512<T>(a, st) : launch_fused<T>(a, st));
-    if (e != cudaSuccess) return e;
-    if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-    if (rows512)
-        e = launch_rows512<T>(a, m, H, false, st);
-    else if (rows1024)
-        e = launch_rows1024(true, a.spec, H, a.nx, a.ny, planes, a.twx, a.log2twx, (float)(-a.Ms), a.out_scale,
-                            a.L, st);
-    else {
-        k_rows_inverse<T><<<grid_rows, kRowThreads, smem_rows, st>>>((const C *)a.spec, H, a.nx, a.ny,
-                                                                     a.log2Px, npair, (const C *)a.twx,
-                                                                     a.log2twx, (T)(-a.Ms),
+    } else {
+        e = cudaFuncSetAttribute(k_rows_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows);
+        if (e != cudaSuccess) return e;
+        k_rows_inverse<T><<<grid_rows, kRowThreads, smem_rows, st>>>((const C *)a.spec, H, a.nx, a.ny, a.log2Px,
+                                                                     npair, (const C *)a.twx, a.log2twx, (T)(-a.Ms),
                                                                      (const T *)a.out_scale, a.L);
-        e = cudaGetLastError();
     }
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t columns_stage(const ApplyArgs &a, cudaStream_t st) {
+    return a.split ? launch_split_columns(a, sizeof(T) == 8, st)
+                   : (a.natural ? launch_cols512<T>(a, st) : launch_fused<T>(a, st));
+}
+
+template <typename T>
+static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t st,
+                              cudaEvent_t *ev) {
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
+    if ((e = rows_stage<T>(a, m, H, true, st)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+    if ((e = columns_stage<T>(a, st)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
+    if ((e = rows_stage<T>(a, m, H, false, st)) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+cudaError_t launch_apply_stage(const ApplyArgs &a, int stage, const void *m, void *H, bool fp64, cudaStream_t st) {
+    if (stage == 1) return fp64 ? columns_stage<double>(a, st) : columns_stage<float>(a, st);
+    if (fp64) return rows_stage<double>(a, (const double *)m, (double *)H, stage == 0, st);
+    return rows_stage<float>(a, (const float *)m, (float *)H, stage == 0, st);
 }
 
 cudaError_t launch_apply(const ApplyArgs &a, const void *m, void *H, bool fp64, cudaStream_t st,

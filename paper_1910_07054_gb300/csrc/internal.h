@@ -146,6 +146,10 @@ int fused_max_layers(bool fp64, int log2Py);
 constexpr int kApplyStages = 3;
 cudaError_t launch_apply(const ApplyArgs &a, const void *m, void *H, bool fp64, cudaStream_t st,
                          cudaEvent_t *events = nullptr);
+// One of the three stages of launch_apply: 0 forward rows (m -> a.spec), 1 the
+// columns with the layer sum (a.spec in place), 2 inverse rows (a.spec -> H);
+// the row stages work on the a.B states at m / H / a.spec as given.
+cudaError_t launch_apply_stage(const ApplyArgs &a, int stage, const void *m, void *H, bool fp64, cudaStream_t st);
 
 }  // namespace demag
 
@@ -174,6 +178,14 @@ struct demag_plan {
     void *d_stage_m = nullptr;    // staging for demag_apply_host
     void *d_stage_H = nullptr;
     unsigned *h_timeouts = nullptr;  // pinned host copy of the two bounded-wait counters
+    cudaStream_t copy_st = nullptr;  // demag_apply_host: input copies of a pipelined batch
+    cudaStream_t copy_st2 = nullptr; // and its output copies
+    // events of the two staging sets: start, 4 inputs, 4 outputs, m staging free,
+    // H staging free
+    cudaEvent_t pipe_ev[2][11] = {};
+    void *d_stage2_m = nullptr;      // second staging set (demag_apply_host_async)
+    void *d_stage2_H = nullptr;
+    int stage_set = 0;               // set of the last demag_apply_host_async
     size_t tensor_bytes = 0, field_bytes_per_state = 0;
     int device = 0;
 };

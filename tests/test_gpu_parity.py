@@ -249,6 +249,48 @@ def test_host_entry_point_512_point_path():
     assert torch.equal(Hh, Hd)
 
 
+@pytest.mark.parametrize("nx,ny,th,prec,B", [
+    (200, 140, (1.0, 0.5, 2.0), dm.PREC_FP32, 5),        # 512-point rows, fused 512-point columns
+    (300, 20, (1.0, 0.5, 2.0, 0.8), dm.PREC_SPLIT_BF16, 3),  # 1024-point rows, split columns
+    (20, 12, (1.0, 0.6), dm.PREC_FP64, 4),                # generic kernels, double
+])
+def test_host_entry_point_pipelined_batch(nx, ny, th, prec, B):
+    """Pinned buffers and a batch: the chunked copies overlapped with the row
+    transforms give the device field bit for bit, call after call; a pageable
+    output buffer takes the plain staged copies."""
+    dtype = torch.float64 if prec == dm.PREC_FP64 else torch.float32
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=prec, max_batch=B)
+    for seed in (51, 52):
+        m = inputs.random_unit_vectors((B, len(th), ny, nx), seed=seed)
+        mh = torch.tensor(m, dtype=dtype).pin_memory()
+        Hh = torch.full_like(mh, float("nan")).pin_memory()
+        dm.demag_apply_host(plan.handle, mh, 3.0, Hh)
+        Hd = plan.apply(mh.cuda(), 3.0).cpu()
+        assert torch.equal(Hh, Hd)
+        Hp = torch.empty_like(mh)  # pageable
+        dm.demag_apply_host(plan.handle, mh, 3.0, Hp)
+        assert torch.equal(Hp, Hd)
+    plan.close()
+
+
+def test_host_entry_point_async_stream_of_batches():
+    """demag_apply_host_async: consecutive batches on alternating host buffers,
+    one wait at the end, every field equal to the device apply bit for bit."""
+    nx, ny, th, B = 300, 20, (1.0, 0.5, 2.0, 0.8), 3
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_BF16, max_batch=B)
+    ms = [inputs.random_unit_vectors((B, len(th), ny, nx), seed=60 + k) for k in range(4)]
+    mh = [torch.tensor(m, dtype=torch.float32).pin_memory() for m in ms]
+    Hh = [torch.full_like(x, float("nan")).pin_memory() for x in mh]
+    for k in range(4):
+        dm.demag_apply_host_async(plan.handle, mh[k], 3.0, Hh[k])
+    dm.demag_apply_host_wait(plan.handle)
+    for k in range(4):
+        assert torch.equal(Hh[k], plan.apply(mh[k].cuda(), 3.0).cpu()), k
+    with pytest.raises(dm.DemagError):
+        dm.demag_apply_host_async(plan.handle, torch.zeros_like(mh[0]), 3.0, Hh[0])  # pageable input
+    plan.close()
+
+
 def test_uniform_film_gpu():
     n, t, Ms = 63, 0.5, 8e5
     m = np.zeros((1, 1, 3, n, n))
