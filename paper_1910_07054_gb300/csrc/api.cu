@@ -163,7 +163,13 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
     for (int l = 0; l < L; ++l) z[l + 1] = z[l] + p->thickness[l];
 
     const int Px = 1 << p->log2Px, Py = 1 << p->log2Py;
-    const size_t plane_bytes = (size_t)3 * Px * Py * sizeof(double2);
+    // Float plans take the values (evaluated in double) through float planes
+    // and float 2D FFTs: the transform's rounding (~1e-7 of the spectrum) is
+    // that of the float tensor they store.  Double plans and the z-offset
+    // kernels of the equidistant method stay in double.
+    const bool f32 = p->precision != DEMAG_PREC_FP64 && !zoffsets;
+    const size_t cpx = f32 ? sizeof(float2) : sizeof(double2);
+    const size_t plane_bytes = (size_t)3 * Px * Py * cpx;
     // pairs per chunk: bounded workspace (~4 GB)
     int chunk = 1;
     {
@@ -175,7 +181,7 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
     }
     int *d_pi = nullptr, *d_pj = nullptr;
     double *d_z = nullptr, *d_th = nullptr;
-    double2 *planes = nullptr, *twx = nullptr, *twy = nullptr;
+    void *planes = nullptr, *twx = nullptr, *twy = nullptr;
     demag_status rc = DEMAG_OK;
     auto cleanup = [&]() {
         cudaFree(d_pi);
@@ -191,17 +197,22 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
         if ((rc = dalloc((void **)&d_pj, pj.size() * sizeof(int), "pair list")) != DEMAG_OK) break;
         if ((rc = dalloc((void **)&d_z, z.size() * sizeof(double), "interfaces")) != DEMAG_OK) break;
         if ((rc = dalloc((void **)&d_th, L * sizeof(double), "thicknesses")) != DEMAG_OK) break;
-        if ((rc = dalloc((void **)&planes, plane_bytes * chunk, "tensor planes")) != DEMAG_OK) break;
+        if ((rc = dalloc(&planes, plane_bytes * chunk, "tensor planes")) != DEMAG_OK) break;
         auto htwx = twiddles<double2>(p->log2Px), htwy = twiddles<double2>(p->log2Py);
-        if ((rc = dalloc((void **)&twx, htwx.size() * sizeof(double2), "twiddles")) != DEMAG_OK) break;
-        if ((rc = dalloc((void **)&twy, htwy.size() * sizeof(double2), "twiddles")) != DEMAG_OK) break;
+        std::vector<float2> ftwx(htwx.size()), ftwy(htwy.size());
+        for (size_t k = 0; k < htwx.size(); ++k) ftwx[k] = make_float2((float)htwx[k].x, (float)htwx[k].y);
+        for (size_t k = 0; k < htwy.size(); ++k) ftwy[k] = make_float2((float)htwy[k].x, (float)htwy[k].y);
+        const void *stwx = f32 ? (const void *)ftwx.data() : (const void *)htwx.data();
+        const void *stwy = f32 ? (const void *)ftwy.data() : (const void *)htwy.data();
+        if ((rc = dalloc(&twx, htwx.size() * cpx, "twiddles")) != DEMAG_OK) break;
+        if ((rc = dalloc(&twy, htwy.size() * cpx, "twiddles")) != DEMAG_OK) break;
         cudaError_t e;
         if ((e = cudaMemcpyAsync(d_pi, pi.data(), pi.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d_pj, pj.data(), pj.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d_z, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d_th, p->thickness.data(), L * sizeof(double), cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(twx, htwx.data(), htwx.size() * sizeof(double2), cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(twy, htwy.data(), htwy.size() * sizeof(double2), cudaMemcpyHostToDevice, st))) {
+            (e = cudaMemcpyAsync(twx, stwx, htwx.size() * cpx, cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(twy, stwy, htwy.size() * cpx, cudaMemcpyHostToDevice, st))) {
             rc = cuda_fail(e, "cudaMemcpyAsync(tensor set-up)");
             break;
         }
@@ -211,21 +222,21 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
                 rc = cuda_fail(e, "cudaMemsetAsync(tensor planes)");
                 break;
             }
-            e = layer < 0 ? launch_kernel_planes(planes, p0, np, d_pi, d_pj, p->nx, p->ny, p->dx, p->dy,
+            e = layer < 0 ? launch_kernel_planes(planes, f32, p0, np, d_pi, d_pj, p->nx, p->ny, p->dx, p->dy,
                                                  p->log2Px, p->log2Py, d_z, d_th, st,
                                                  p->precision != DEMAG_PREC_FP64)
-                          : launch_dkernel_planes(planes, p0, np, L, layer, p->nx, p->ny, p->dx, p->dy,
+                          : launch_dkernel_planes(planes, f32, p0, np, L, layer, p->nx, p->ny, p->dx, p->dy,
                                                   p->log2Px, p->log2Py, d_z, d_th, st);
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "tensor evaluation kernel");
                 break;
             }
-            if ((e = launch_fft2_planes(planes, 3 * np, p->log2Px, p->log2Py, twx, p->log2Px, twy,
+            if ((e = launch_fft2_planes(planes, f32, 3 * np, p->log2Px, p->log2Py, twx, p->log2Px, twy,
                                         p->log2Py, st)) != cudaSuccess) {
                 rc = cuda_fail(e, "tensor FFT kernels");
                 break;
             }
-            if ((e = launch_extract_tensor(planes, p0, np, npairs, p->log2Px, p->log2Py,
+            if ((e = launch_extract_tensor(planes, f32, p0, np, npairs, p->log2Px, p->log2Py,
                                            zoffsets ? tensor_row(p->log2Py, true) : p->QyS, dst,
                                            zoffsets || p->precision == DEMAG_PREC_FP64, st,
                                            zoffsets ? 0 : (layer < 0 ? p->umajor : 0),

@@ -40,7 +40,15 @@ __device__ __forceinline__ int bit_reverse(int v, int log2n) {
     return (int)(__brev((unsigned)v) >> (32 - log2n));
 }
 
-template <bool INV, typename C>
+// Position of element i of a column in shared memory: i itself, or with PAD > 0
+// one slot of padding after every 2^PAD elements (spreads a bit-reversed
+// scatter of 16-byte elements over the banks).
+template <int PAD>
+__device__ __forceinline__ int fft_pos(int i) {
+    return PAD ? i + (i >> PAD) : i;
+}
+
+template <bool INV, typename C, int PAD = 0>
 __device__ void fft_dit(C *buf, int log2n, int ncols, int col_stride, const C *__restrict__ tw,
                         int log2tw) {
     const int n = 1 << log2n;
@@ -56,8 +64,10 @@ __device__ void fft_dit(C *buf, int log2n, int ncols, int col_stride, const C *_
             const int bf = idx & ((1 << lq) - 1);
             const int j = bf & (h - 1);
             const int g = (bf >> s) << (s + 2);
-            C *p = buf + col * col_stride + g + j;
-            C x0 = p[0], x1 = p[h], x2 = p[2 * h], x3 = p[3 * h];
+            C *p = buf + col * col_stride;
+            const int i0 = fft_pos<PAD>(g + j), i1 = fft_pos<PAD>(g + j + h), i2 = fft_pos<PAD>(g + j + 2 * h),
+                      i3 = fft_pos<PAD>(g + j + 3 * h);
+            C x0 = p[i0], x1 = p[i1], x2 = p[i2], x3 = p[i3];
             const C w1 = twiddle<INV>(tw, j << (sh2 + 1));  // W_{2h}^j
             const C w2 = twiddle<INV>(tw, j << sh2);        // W_{4h}^j
             C t1 = c_mul(w1, x1), t3 = c_mul(w1, x3);
@@ -65,10 +75,10 @@ __device__ void fft_dit(C *buf, int log2n, int ncols, int col_stride, const C *_
             C a2 = c_add(x2, t3), a3 = c_sub(x2, t3);
             C u2 = c_mul(w2, a2);
             C u3 = c_quarter<INV>(c_mul(w2, a3));  // W_{4h}^{j+h} = W_{4h}^j * W_4
-            p[0] = c_add(a0, u2);
-            p[2 * h] = c_sub(a0, u2);
-            p[h] = c_add(a1, u3);
-            p[3 * h] = c_sub(a1, u3);
+            p[i0] = c_add(a0, u2);
+            p[i2] = c_sub(a0, u2);
+            p[i1] = c_add(a1, u3);
+            p[i3] = c_sub(a1, u3);
         }
         __syncthreads();
     }
@@ -79,11 +89,12 @@ __device__ void fft_dit(C *buf, int log2n, int ncols, int col_stride, const C *_
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int col = idx >> s;
             const int j = idx & (h - 1);
-            C *p = buf + col * col_stride + j;
-            C t = c_mul(twiddle<INV>(tw, j << sh), p[h]);
-            C a = p[0];
-            p[0] = c_add(a, t);
-            p[h] = c_sub(a, t);
+            C *p = buf + col * col_stride;
+            const int i0 = fft_pos<PAD>(j), i1 = fft_pos<PAD>(j + h);
+            C t = c_mul(twiddle<INV>(tw, j << sh), p[i1]);
+            C a = p[i0];
+            p[i0] = c_add(a, t);
+            p[i1] = c_sub(a, t);
         }
         __syncthreads();
     }

@@ -33,10 +33,11 @@ struct StackDev {
 cudaError_t launch_tensor_points(int n, const double *geom, double *out, cudaStream_t st);
 
 // Fill the padded real-space kernels of pairs [p0, p0 + np) into three complex
-// double planes per pair ([np][3][Py][Px], x fastest), zeroed beforehand:
-// plane 0 = N_xx + i N_yy, plane 1 = N_zz + i N_xy, plane 2 = N_xz + i N_yz.
-// far32: far-field quadrature with float node sums (float plans).
-cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pair_i,
+// planes per pair ([np][3][Py][Px], x fastest; float2 if f32, else double2),
+// zeroed beforehand: plane 0 = N_xx + i N_yy, plane 1 = N_zz + i N_xy, plane 2 =
+// N_xz + i N_yz; every value is evaluated in double.  far32: far-field
+// quadrature with float node sums (float plans).
+cudaError_t launch_kernel_planes(void *planes, bool f32, int p0, int np, const int *pair_i,
                                  const int *pair_j, int nx, int ny, double dx, double dy,
                                  int log2Px, int log2Py, const double *z, const double *th,
                                  cudaStream_t st, bool far32 = false);
@@ -48,20 +49,20 @@ cudaError_t launch_tensor_points_dt(int n, const double *geom, double *out, doub
 
 // d N(i <- j)/d t_layer of all L*L pairs P = i*L + j in [p0, p0 + np), as
 // three complex planes per pair like launch_kernel_planes (zeroed beforehand).
-cudaError_t launch_dkernel_planes(double2 *planes, int p0, int np, int L, int layer, int nx, int ny,
+cudaError_t launch_dkernel_planes(void *planes, bool f32, int p0, int np, int L, int layer, int nx, int ny,
                                   double dx, double dy, int log2Px, int log2Py, const double *z,
                                   const double *th, cudaStream_t st);
 
-// In-place 2D FFT (forward, double) of nplanes planes [Py][Px].
-cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log2Py,
-                               const double2 *twx, int log2twx, const double2 *twy, int log2twy,
-                               cudaStream_t st);
+// In-place 2D FFT (forward) of nplanes planes [Py][Px] of float2 (f32, with
+// float twiddle tables) or double2.
+cudaError_t launch_fft2_planes(void *planes, bool f32, int nplanes, int log2Px, int log2Py, const void *twx,
+                               int log2twx, const void *twy, int log2twy, cudaStream_t st);
 
 // Extract the stored quadrant of pairs [p0, p0+np) from transformed planes into
 // the plan tensor, scaled by 1/(Px Py), y-frequencies in the stored order of
 // layout.cuh: [Kx][npairs][6][QyS] (umajor = 0) or [Kx][Qy][npairs][6]
 // (umajor = 1, float only).
-cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs,
+cudaError_t launch_extract_tensor(const void *planes, bool f32, int p0, int np, int npairs,
                                   int log2Px, int log2Py, int QyS, void *tensor, bool fp64,
                                   cudaStream_t st, int umajor = 0, int natural = 0);
 

@@ -400,11 +400,9 @@ __device__ __forceinline__ void axis_nodes_f(const AxisRuleF &r, int n, float of
         }
 }
 
-__device__ bool quadrature_tensor_f32(double Xd, double Yd, double Zd, const double t[3], const double s[3],
-                                      double gap, double out[6]) {
-    const float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
-    const float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
-    const float gapf = (float)gap, wcap = 0.5f * gapf, inv_wcap = 1.f / wcap;
+// Nodes per sub-piece of the float quadrature from rho = gap / widest sub-piece
+// (sub-pieces no wider than half the gap).
+__device__ __forceinline__ int f32_nodes(const float tf[3], const float sf[3], float gapf, float inv_wcap) {
     float widest = 0.f;
     for (int k = 0; k < 3; ++k) {
         const float br0 = -sf[k], br1 = fminf(0.f, tf[k] - sf[k]), br2 = fmaxf(0.f, tf[k] - sf[k]), br3 = tf[k];
@@ -413,7 +411,15 @@ __device__ bool quadrature_tensor_f32(double Xd, double Yd, double Zd, const dou
             if (ws[p] > 0.f) widest = fmaxf(widest, ws[p] / ceilf(ws[p] * inv_wcap));
     }
     const float rho = gapf / widest;
-    const int n = rho >= 64.f ? 2 : rho >= 11.f ? 3 : rho >= 4.f ? 4 : rho >= 2.75f ? 5 : 6;
+    return rho >= 64.f ? 2 : rho >= 11.f ? 3 : rho >= 4.f ? 4 : rho >= 2.75f ? 5 : 6;
+}
+
+__device__ bool quadrature_tensor_f32(double Xd, double Yd, double Zd, const double t[3], const double s[3],
+                                      double gap, double out[6]) {
+    const float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
+    const float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
+    const float gapf = (float)gap, wcap = 0.5f * gapf, inv_wcap = 1.f / wcap;
+    const int n = f32_nodes(tf, sf, gapf, inv_wcap);
     AxisRuleF rx, ry, rz;
     axis_rule_f(rx, tf[0], sf[0], inv_wcap, n);
     axis_rule_f(ry, tf[1], sf[1], inv_wcap, n);
@@ -596,9 +602,92 @@ __device__ void quadrature_tensor_dt(double X, double Y, double Z, const double 
     }
 }
 
-// Value and derivative of the evaluation used everywhere (tensor_eval).
+// The derivative of quadrature_tensor_dt entirely in float, with the node
+// counts of quadrature_tensor_f32, for float plans.  dN = sc (dI - I dtz / tz)
+// is linear in the node weights, so the trapezoid-weighted z nodes of I (scaled
+// by -dtz / tz) and the derivative-interval nodes of dI form one z list and one
+// sum.  Returns false (nothing written) if an axis needs more than kF32AxisMax
+// nodes or the z list more than 2 kF32AxisMax.
+__device__ bool quadrature_tensor_dt_f32(double Xd, double Yd, double Zd, const double t[3], const double s[3],
+                                         double gap, double dtz, double dsz, double dZ, double dout[6]) {
+    const float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
+    const float sf[3] = {(float)s[0], (float)s[1], (float)s[2]};
+    const float gapf = (float)gap, wcap = 0.5f * gapf, inv_wcap = 1.f / wcap;
+    const int n = f32_nodes(tf, sf, gapf, inv_wcap);
+    AxisRuleF rx, ry, rz;
+    axis_rule_f(rx, tf[0], sf[0], inv_wcap, n);
+    axis_rule_f(ry, tf[1], sf[1], inv_wcap, n);
+    if (rx.count > kF32AxisMax || ry.count > kF32AxisMax) return false;
+    float xd[kF32AxisMax], xw[kF32AxisMax], yd[kF32AxisMax], yw[kF32AxisMax];
+    float zd[2 * kF32AxisMax], zw[2 * kF32AxisMax];
+    int nz = 0;
+    const float a = tf[2], b = sf[2], Zf = (float)Zd;
+    if (dtz != 0.0) {
+        axis_rule_f(rz, a, b, inv_wcap, n);
+        if (rz.count > kF32AxisMax) return false;
+        axis_nodes_f(rz, n, Zf, zd, zw);
+        const float f = (float)(-dtz / t[2]);
+        for (int k = 0; k < rz.count; ++k) zw[k] *= f;
+        nz = rz.count;
+    }
+    // dI/da, dI/db and dI/dZ as plain integrals of Phi over sub-intervals of [-b, a]
+    const float lo[4] = {a - b, -b, fmaxf(0.f, a - b), -b};
+    const float hi[4] = {a, a - b, a, fminf(0.f, a - b)};
+    const float cf[4] = {(float)dtz, (float)dsz, (float)dZ, (float)-dZ};
+    for (int iv = 0; iv < 4; ++iv) {
+        const float w = hi[iv] - lo[iv];
+        if (cf[iv] == 0.f || !(w > 0.f)) continue;
+        const int cuts = (int)ceilf(w * inv_wcap);
+        if (nz + cuts * n > 2 * kF32AxisMax) return false;
+        const float len = w / (float)cuts, half = 0.5f * len;
+        for (int c = 0; c < cuts; ++c) {
+            const float mid = lo[iv] + len * (float)c + half;
+            for (int i = 0; i < n; ++i, ++nz) {
+                zd[nz] = Zf + mid + half * c_gl_xf[n][i];
+                zw[nz] = half * c_gl_wf[n][i] * cf[iv];
+            }
+        }
+    }
+    axis_nodes_f(rx, n, (float)Xd, xd, xw);
+    axis_nodes_f(ry, n, (float)Yd, yd, yw);
+    float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+    for (int kx = 0; kx < rx.count; ++kx) {
+        const float dxv = xd[kx], wx = xw[kx];
+        for (int ky = 0; ky < ry.count; ++ky) {
+            const float dyv = yd[ky];
+            const float wxy = wx * yw[ky];
+            const float rxy = dxv * dxv + dyv * dyv;
+            for (int kz = 0; kz < nz; ++kz) {
+                const float dzv = zd[kz];
+                const float r2 = rxy + dzv * dzv;
+                const float ir = rsqrtf(r2);
+                const float ir2 = ir * ir;
+                const float q = wxy * zw[kz] * ir * ir2 * ir2;
+                const float q3 = 3.f * q;
+                hxx += q3 * dxv * dxv - q * r2;
+                hyy += q3 * dyv * dyv - q * r2;
+                hzz += q3 * dzv * dzv - q * r2;
+                hxy += q3 * dxv * dyv;
+                hxz += q3 * dxv * dzv;
+                hyz += q3 * dyv * dzv;
+            }
+        }
+    }
+    const double sc = -1.0 / (4.0 * kPi * t[0] * t[1] * t[2]);
+    dout[0] = hxx * sc;
+    dout[1] = hyy * sc;
+    dout[2] = hzz * sc;
+    dout[3] = hxy * sc;
+    dout[4] = hxz * sc;
+    dout[5] = hyz * sc;
+    return true;
+}
+
+// Value and derivative of the evaluation used everywhere (tensor_eval).  With
+// far32, far offsets take quadrature_tensor_dt_f32 and only dout is written.
 __device__ void tensor_eval_dt(double X, double Y, double Z, const double t[3], const double s[3],
-                               double dtz, double dsz, double dZ, double out[6], double dout[6]) {
+                               double dtz, double dsz, double dZ, double out[6], double dout[6],
+                               bool far32 = false) {
     const double o[3] = {X, Y, Z};
     double gap2 = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -619,6 +708,7 @@ __device__ void tensor_eval_dt(double X, double Y, double Z, const double t[3], 
         }
         return;
     }
+    if (far32 && quadrature_tensor_dt_f32(X, Y, Z, t, s, gap, dtz, dsz, dZ, dout)) return;
     const double wcap = 0.5 * gap;
     double widest = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -652,7 +742,16 @@ cudaError_t launch_tensor_points(int n, const double *geom, double *out, cudaStr
 // Write N at offset (p, q) of a pair's three planes, with the parity of each
 // component in X and Y (f even, g odd in x and y), at the up to four mirrored
 // positions of the circulant grid.
-__device__ __forceinline__ void write_planes(double2 *base, int p, int q, int Px, int Py, const double N[6]) {
+template <typename C>
+__device__ __forceinline__ C plane_val(double a, double b) {
+    C v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
+
+template <typename C>
+__device__ __forceinline__ void write_planes(C *base, int p, int q, int Px, int Py, const double N[6]) {
     for (int my = 0; my < 2; ++my) {
         if (my && q == 0) continue;
         const int yi = my ? Py - q : q;
@@ -662,9 +761,9 @@ __device__ __forceinline__ void write_planes(double2 *base, int p, int q, int Px
             const int xi = mx ? Px - p : p;
             const double sgx = mx ? -1.0 : 1.0;
             const size_t o = (size_t)yi * Px + xi;
-            base[o] = make_double2(N[0], N[1]);
-            base[(size_t)Px * Py + o] = make_double2(N[2], sgx * sgy * N[3]);
-            base[(size_t)2 * Px * Py + o] = make_double2(sgx * N[4], sgy * N[5]);
+            base[o] = plane_val<C>(N[0], N[1]);
+            base[(size_t)Px * Py + o] = plane_val<C>(N[2], sgx * sgy * N[3]);
+            base[(size_t)2 * Px * Py + o] = plane_val<C>(sgx * N[4], sgy * N[5]);
         }
     }
 }
@@ -673,7 +772,8 @@ __device__ __forceinline__ void write_planes(double2 *base, int p, int q, int Px
 // the 6 x 64 signed Newell terms (closed_nxx / closed_nxy with their axis
 // permutations) are spread over the lanes, 12 each, and summed by a warp
 // reduction; offsets that are not near return (k_kernel_planes has them).
-__global__ void __launch_bounds__(32) k_near_planes(double2 *__restrict__ planes, int p0, int np,
+template <typename C>
+__global__ void __launch_bounds__(32) k_near_planes(C *__restrict__ planes, int p0, int np,
                                                     const int *__restrict__ pair_i,
                                                     const int *__restrict__ pair_j, int nx, int ny, double dx,
                                                     double dy, int log2Px, int log2Py,
@@ -726,7 +826,8 @@ __global__ void __launch_bounds__(32) k_near_planes(double2 *__restrict__ planes
 // One thread per (pair, q, p) with 0 <= p < nx, 0 <= q < ny: evaluate N(i <- j)
 // at (p dx, q dy, z_i - z_j) and write it (write_planes); near offsets are
 // k_near_planes'.
-__global__ void k_kernel_planes(double2 *__restrict__ planes, int p0, int np,
+template <typename C>
+__global__ void k_kernel_planes(C *__restrict__ planes, int p0, int np,
                                 const int *__restrict__ pair_i, const int *__restrict__ pair_j,
                                 int nx, int ny, double dx, double dy, int log2Px, int log2Py,
                                 const double *__restrict__ z, const double *__restrict__ th,
@@ -768,8 +869,10 @@ cudaError_t launch_tensor_points_dt(int n, const double *geom, double *out, doub
 // d N(i <- j) / d t_layer for all L*L pairs (P = i*L + j) of [p0, p0 + np),
 // written with the in-plane parity like k_kernel_planes.  Seeds: the target
 // edge moves if i == layer, the source edge if j == layer, and the offset
-// z_i - z_j by [i > layer] - [j > layer].
-__global__ void k_dkernel_planes(double2 *__restrict__ planes, int p0, int np, int L, int layer,
+// z_i - z_j by [i > layer] - [j > layer].  Float planes (float plans) take the
+// far field in float.
+template <typename C>
+__global__ void k_dkernel_planes(C *__restrict__ planes, int p0, int np, int L, int layer,
                                  int nx, int ny, double dx, double dy, int log2Px, int log2Py,
                                  const double *__restrict__ z, const double *__restrict__ th) {
     const int cpr = (nx + blockDim.x - 1) / blockDim.x;  // blocks as in k_kernel_planes
@@ -782,23 +885,9 @@ __global__ void k_dkernel_planes(double2 *__restrict__ planes, int p0, int np, i
     if (dtz == 0.0 && dsz == 0.0 && dZ == 0.0) return;  // planes are zeroed beforehand
     const double t[3] = {dx, dy, th[i]}, s[3] = {dx, dy, th[j]};
     double N[6], dN[6];
-    tensor_eval_dt(p * dx, q * dy, z[i] - z[j], t, s, dtz, dsz, dZ, N, dN);
+    tensor_eval_dt(p * dx, q * dy, z[i] - z[j], t, s, dtz, dsz, dZ, N, dN, sizeof(C) == sizeof(float2));
     const int Px = 1 << log2Px, Py = 1 << log2Py;
-    double2 *base = planes + (size_t)P * 3 * Px * Py;
-    for (int my = 0; my < 2; ++my) {
-        if (my && q == 0) continue;
-        const int yi = my ? Py - q : q;
-        const double sgy = my ? -1.0 : 1.0;
-        for (int mx = 0; mx < 2; ++mx) {
-            if (mx && p == 0) continue;
-            const int xi = mx ? Px - p : p;
-            const double sgx = mx ? -1.0 : 1.0;
-            const size_t o = (size_t)yi * Px + xi;
-            base[o] = make_double2(dN[0], dN[1]);
-            base[(size_t)Px * Py + o] = make_double2(dN[2], sgx * sgy * dN[3]);
-            base[(size_t)2 * Px * Py + o] = make_double2(sgx * dN[4], sgy * dN[5]);
-        }
-    }
+    write_planes(planes + (size_t)P * 3 * Px * Py, p, q, Px, Py, dN);
 }
 
 // Grid of the plane kernels: x = pair, y = (row q, chunk of 128 offsets p).  The
@@ -808,57 +897,85 @@ __global__ void k_dkernel_planes(double2 *__restrict__ planes, int p0, int np, i
 // and on different SMs instead of queueing behind one another.
 static dim3 plane_grid(int np, int nx, int ny, int bs) { return dim3(np, ny * ((nx + bs - 1) / bs)); }
 
-cudaError_t launch_dkernel_planes(double2 *planes, int p0, int np, int L, int layer, int nx, int ny,
+cudaError_t launch_dkernel_planes(void *planes, bool f32, int p0, int np, int L, int layer, int nx, int ny,
                                   double dx, double dy, int log2Px, int log2Py, const double *z,
                                   const double *th, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
-    k_dkernel_planes<<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(planes, p0, np, L, layer, nx, ny, dx, dy,
-                                                                 log2Px, log2Py, z, th);
+    if (f32)
+        k_dkernel_planes<float2><<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(
+            (float2 *)planes, p0, np, L, layer, nx, ny, dx, dy, log2Px, log2Py, z, th);
+    else
+        k_dkernel_planes<double2><<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(
+            (double2 *)planes, p0, np, L, layer, nx, ny, dx, dy, log2Px, log2Py, z, th);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kernel_planes(double2 *planes, int p0, int np, const int *pair_i,
-                                 const int *pair_j, int nx, int ny, double dx, double dy,
-                                 int log2Px, int log2Py, const double *z, const double *th,
+template <typename C>
+static cudaError_t kernel_planes(C *planes, int p0, int np, const int *pair_i, const int *pair_j, int nx, int ny,
+                                 double dx, double dy, int log2Px, int log2Py, const double *z, const double *th,
                                  cudaStream_t st, bool far32) {
-    if (np <= 0) return cudaSuccess;
     // near offsets: gap >= (p - 1) dx along x (and likewise y), so only
     // p <= ceil(e / dx), q <= ceil(e / dy) can be below e = max(dx, dy)
     const double e = dx > dy ? dx : dy;
     const int pm = (int)ceil(e / dx), qm = (int)ceil(e / dy);
-    k_near_planes<<<dim3(np, (pm + 1) * (qm + 1)), 32, 0, st>>>(planes, p0, np, pair_i, pair_j, nx, ny, dx, dy,
-                                                                log2Px, log2Py, z, th, pm);
+    k_near_planes<C><<<dim3(np, (pm + 1) * (qm + 1)), 32, 0, st>>>(planes, p0, np, pair_i, pair_j, nx, ny, dx,
+                                                                   dy, log2Px, log2Py, z, th, pm);
     cudaError_t e1 = cudaGetLastError();
     if (e1 != cudaSuccess) return e1;
-    k_kernel_planes<<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(planes, p0, np, pair_i, pair_j, nx, ny, dx, dy,
-                                                                log2Px, log2Py, z, th, far32 ? 1 : 0);
+    k_kernel_planes<C><<<plane_grid(np, nx, ny, 128), 128, 0, st>>>(planes, p0, np, pair_i, pair_j, nx, ny, dx,
+                                                                   dy, log2Px, log2Py, z, th, far32 ? 1 : 0);
     return cudaGetLastError();
 }
 
+cudaError_t launch_kernel_planes(void *planes, bool f32, int p0, int np, const int *pair_i,
+                                 const int *pair_j, int nx, int ny, double dx, double dy,
+                                 int log2Px, int log2Py, const double *z, const double *th,
+                                 cudaStream_t st, bool far32) {
+    if (np <= 0) return cudaSuccess;
+    return f32 ? kernel_planes((float2 *)planes, p0, np, pair_i, pair_j, nx, ny, dx, dy, log2Px, log2Py, z, th,
+                               st, far32)
+               : kernel_planes((double2 *)planes, p0, np, pair_i, pair_j, nx, ny, dx, dy, log2Px, log2Py, z, th,
+                               st, far32);
+}
+
 // Row FFTs of [nrows][Px] complex double, rows_per_block rows per block.
-__global__ void k_fft_rows_f64(double2 *__restrict__ data, long long nrows, int log2n,
-                               int rows_per_block, const double2 *__restrict__ tw, int log2tw) {
-    extern __shared__ double2 sm_rows[];
+// Row FFTs: each row is loaded in natural order and scattered to its
+// bit-reversed positions; a padding slot after every 128 elements keeps the
+// eight 16-byte writes of a quarter warp (bit-reversed positions 128 apart) in
+// distinct banks.
+constexpr int kRowPad = 7;
+
+template <typename C>
+__global__ void k_fft_rows_f64(C *__restrict__ data, long long nrows, int log2n, int rows_per_block,
+                               const C *__restrict__ tw, int log2tw) {
+    extern __shared__ __align__(16) unsigned char sm_rows_raw[];
+    C *sm_rows = reinterpret_cast<C *>(sm_rows_raw);
     const int n = 1 << log2n;
+    const int stride = n + (n >> kRowPad);
     const long long r0 = (long long)blockIdx.x * rows_per_block;
     const int nr = (int)min((long long)rows_per_block, nrows - r0);
     for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
         const int r = e >> log2n, x = e & (n - 1);
-        sm_rows[r * n + bit_reverse(x, log2n)] = data[(size_t)(r0 + r) * n + x];
+        sm_rows[r * stride + fft_pos<kRowPad>(bit_reverse(x, log2n))] = data[(size_t)(r0 + r) * n + x];
     }
     __syncthreads();
-    fft_dit<false>(sm_rows, log2n, nr, n, tw, log2tw);
-    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) data[(size_t)r0 * n + e] = sm_rows[e];
+    fft_dit<false, C, kRowPad>(sm_rows, log2n, nr, stride, tw, log2tw);
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+        const int r = e >> log2n, x = e & (n - 1);
+        data[(size_t)r0 * n + e] = sm_rows[r * stride + fft_pos<kRowPad>(x)];
+    }
 }
 
 // Column FFTs of planes [nplanes][Py][Px]: a block takes `tile` adjacent columns.
-__global__ void k_fft_cols_f64(double2 *__restrict__ data, int log2Px, int log2Py, int tile,
-                               int tiles_per_plane, const double2 *__restrict__ tw, int log2tw) {
-    extern __shared__ double2 sm_cols[];
+template <typename C>
+__global__ void k_fft_cols_f64(C *__restrict__ data, int log2Px, int log2Py, int tile, int tiles_per_plane,
+                               const C *__restrict__ tw, int log2tw) {
+    extern __shared__ __align__(16) unsigned char sm_cols_raw[];
+    C *sm_cols = reinterpret_cast<C *>(sm_cols_raw);
     const int Px = 1 << log2Px, Py = 1 << log2Py;
     const int plane = blockIdx.x / tiles_per_plane;
     const int x0 = (blockIdx.x % tiles_per_plane) * tile;
-    double2 *base = data + (size_t)plane * Px * Py + x0;
+    C *base = data + (size_t)plane * Px * Py + x0;
     const int stride = Py + 1;
     for (int e = threadIdx.x; e < tile * Py; e += blockDim.x) {
         const int y = e / tile, c = e - y * tile;
@@ -872,37 +989,50 @@ __global__ void k_fft_cols_f64(double2 *__restrict__ data, int log2Px, int log2P
     }
 }
 
-cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log2Py,
-                               const double2 *twx, int log2twx, const double2 *twy, int log2twy,
-                               cudaStream_t st) {
+template <typename C>
+static cudaError_t fft2_planes(C *planes, int nplanes, int log2Px, int log2Py, const C *twx, int log2twx,
+                               const C *twy, int log2twy, cudaStream_t st) {
     const int Px = 1 << log2Px, Py = 1 << log2Py;
-    const int budget = 8192;  // complex doubles of shared memory per block (128 KB)
-    int rpb = budget / Px;
+    // 32 KB of shared memory per block: several blocks per SM hide the
+    // global-memory latency of the load and store phases
+    const int budget = (32 << 10) / (int)sizeof(C);
+    const int rstride = Px + (Px >> kRowPad);
+    int rpb = budget / rstride;
     if (rpb < 1) rpb = 1;
     const long long nrows = (long long)nplanes * Py;
-    size_t smem = (size_t)rpb * Px * sizeof(double2);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_rows_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    size_t smem = (size_t)rpb * rstride * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_rows_f64<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_rows_f64<<<(unsigned)((nrows + rpb - 1) / rpb), 256, smem, st>>>(planes, nrows, log2Px, rpb,
-                                                                         twx, log2twx);
+    k_fft_rows_f64<C><<<(unsigned)((nrows + rpb - 1) / rpb), 256, smem, st>>>(planes, nrows, log2Px, rpb, twx,
+                                                                               log2twx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int tile = budget / (Py + 1);
+    // columns: 64 KB blocks of up to 8 adjacent columns (128-byte row pieces in double)
+    int tile = (64 << 10) / (int)sizeof(C) / (Py + 1);
+    if (tile > 8) tile = 8;
     if (tile > Px) tile = Px;
+    if (tile < 1) tile = 1;
     int t2 = 1;
     while (t2 * 2 <= tile) t2 *= 2;
     tile = t2;
-    smem = (size_t)tile * (Py + 1) * sizeof(double2);
-    e = cudaFuncSetAttribute(k_fft_cols_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem = (size_t)tile * (Py + 1) * sizeof(C);
+    e = cudaFuncSetAttribute(k_fft_cols_f64<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // only the columns kx <= Px/2 that k_extract reads: each packed plane holds two
     // components whose spectra are both real or both imaginary (their parities
     // in x and y), so no Hermitian partner at Px - kx is needed
     const int ntile = (Px / 2 + 1 + tile - 1) / tile;  // tile <= Px/2 or tile = Px: inside the plane
-    k_fft_cols_f64<<<(unsigned)((long long)nplanes * ntile), 256, smem, st>>>(planes, log2Px, log2Py, tile,
-                                                                              ntile, twy, log2twy);
+    k_fft_cols_f64<C><<<(unsigned)((long long)nplanes * ntile), 256, smem, st>>>(planes, log2Px, log2Py, tile,
+                                                                                 ntile, twy, log2twy);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fft2_planes(void *planes, bool f32, int nplanes, int log2Px, int log2Py, const void *twx,
+                               int log2twx, const void *twy, int log2twy, cudaStream_t st) {
+    return f32 ? fft2_planes((float2 *)planes, nplanes, log2Px, log2Py, (const float2 *)twx, log2twx,
+                             (const float2 *)twy, log2twy, st)
+               : fft2_planes((double2 *)planes, nplanes, log2Px, log2Py, (const double2 *)twx, log2twx,
+                             (const double2 *)twy, log2twy, st);
 }
 
 // Quadrant kx <= Px/2, ky <= Py/2 of the transformed planes -> plan tensor,
@@ -910,8 +1040,8 @@ cudaError_t launch_fft2_planes(double2 *planes, int nplanes, int log2Px, int log
 // plane 0 = FFT(N_xx) + i FFT(N_yy), both real; plane 1 = FFT(N_zz) + i FFT(N_xy),
 // both real; plane 2 = FFT(N_xz) + i FFT(N_yz) = i a - b with FFT(N_xz) = i a,
 // FFT(N_yz) = i b.
-template <typename T>
-__global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, int npairs,
+template <typename T, typename C>
+__global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npairs,
                           int log2Px, int log2Py, int QyS, T *__restrict__ tensor, int umajor,
                           int natural) {
     const int Px = 1 << log2Px, Py = 1 << log2Py;
@@ -923,8 +1053,10 @@ __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, in
     const int kx = (int)((idx / Qy) % Kx);
     const int P = (int)(idx / ((long long)Qy * Kx));
     const int kq = natural ? u : u_kyq(u, log2Py);
-    const double2 *base = planes + (size_t)P * 3 * Px * Py + (size_t)kq * Px + kx;
-    const double2 A = base[0], Bp = base[(size_t)Px * Py], C = base[(size_t)2 * Px * Py];
+    const C *base = planes + (size_t)P * 3 * Px * Py + (size_t)kq * Px + kx;
+    const double2 A = make_double2(base[0].x, base[0].y);
+    const double2 Bp = make_double2(base[(size_t)Px * Py].x, base[(size_t)Px * Py].y);
+    const double2 Cc = make_double2(base[(size_t)2 * Px * Py].x, base[(size_t)2 * Px * Py].y);
     const double sc = 1.0 / ((double)Px * (double)Py);
     const size_t cs = umajor ? (size_t)umajor_row(npairs) : QyS;  // component stride
     T *o = umajor ? tensor + ((size_t)kx * Qy + u) * umajor_block(npairs) + (size_t)(p0 + P)
@@ -933,21 +1065,30 @@ __global__ void k_extract(const double2 *__restrict__ planes, int p0, int np, in
     o[1 * cs] = (T)(A.y * sc);
     o[2 * cs] = (T)(Bp.x * sc);
     o[3 * cs] = (T)(Bp.y * sc);
-    o[4 * cs] = (T)(C.y * sc);
-    o[5 * cs] = (T)(-C.x * sc);
+    o[4 * cs] = (T)(Cc.y * sc);
+    o[5 * cs] = (T)(-Cc.x * sc);
 }
 
-cudaError_t launch_extract_tensor(const double2 *planes, int p0, int np, int npairs, int log2Px,
+cudaError_t launch_extract_tensor(const void *planes, bool f32, int p0, int np, int npairs, int log2Px,
                                   int log2Py, int QyS, void *tensor, bool fp64, cudaStream_t st,
                                   int umajor, int natural) {
     const long long total = (long long)np * ((1 << log2Px) / 2 + 1) * ((1 << log2Py) / 2 + 1);
     const unsigned grid = (unsigned)((total + 255) / 256);
-    if (fp64)
-        k_extract<double><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
-                                                (double *)tensor, umajor, natural);
-    else
-        k_extract<float><<<grid, 256, 0, st>>>(planes, p0, np, npairs, log2Px, log2Py, QyS,
-                                               (float *)tensor, umajor, natural);
+    if (f32) {
+        if (fp64)
+            k_extract<double, float2><<<grid, 256, 0, st>>>((const float2 *)planes, p0, np, npairs, log2Px, log2Py,
+                                                            QyS, (double *)tensor, umajor, natural);
+        else
+            k_extract<float, float2><<<grid, 256, 0, st>>>((const float2 *)planes, p0, np, npairs, log2Px, log2Py,
+                                                           QyS, (float *)tensor, umajor, natural);
+    } else {
+        if (fp64)
+            k_extract<double, double2><<<grid, 256, 0, st>>>((const double2 *)planes, p0, np, npairs, log2Px,
+                                                             log2Py, QyS, (double *)tensor, umajor, natural);
+        else
+            k_extract<float, double2><<<grid, 256, 0, st>>>((const double2 *)planes, p0, np, npairs, log2Px,
+                                                            log2Py, QyS, (float *)tensor, umajor, natural);
+    }
     return cudaGetLastError();
 }
 
