@@ -137,7 +137,7 @@ demag_status demag_debug_fail_alloc(int after);
  *   precision  a demag_precision value; DEMAG_PREC_SPLIT_TF32 and
  *              DEMAG_PREC_SPLIT_BF16 need (6 L^2 + 12 L B + 12 L B) floats (L padded to 16, B to 8)
  *              within 220 KB of shared memory, and its tensor is stored in
- *              the layout [kx][u][component][pair] (see demag_plan_tensor)
+ *              the blocked layout of demag_plan_tensor
  *   max_batch  largest batch B later passed to demag_apply, >= 1
  *   stream     stream for the set-up work; the call synchronises this stream
  *              before it returns
@@ -365,9 +365,12 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
  *
  * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,
  * layout [kx][pair][component][u] (split-precision plans:
- * (Px/2+1) * (Py/2+1) * NB floats, layout [kx][u][component][pair] with
- * each component row npairs rounded up to a multiple of 4 (NB = 6 times
- * that), the padding zero)
+ * (Px/2+1) * (Py/2+1) * NB floats, layout [kx][u][component][block][row][col]
+ * with nb = ceil(L/8) layer blocks and NB = 6 * 64 * nb (nb + 1) / 2: each
+ * component row holds the 8 x 8 blocks (R <= C) of M(i, j) = (t_i / t_0)
+ * N(i <- j), block row by block row, element (i mod 8, j mod 8) of block
+ * (i / 8, j / 8); a diagonal block holds both triangles, M(i, j) for i > j
+ * being M(j, i) with the xz and yz components negated; layers past L zero)
  * with pair (i <= j) numbered row by row
  * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components
  * {Re N_xx, Re N_yy, Re N_zz, Re N_xy, Im N_xz, Im N_yz} of the 2D DFT of

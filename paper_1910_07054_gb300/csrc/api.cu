@@ -159,6 +159,7 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
             }
     }
     const int npairs = zoffsets ? L : (layer < 0 ? p->npairs : L * L);
+    const int blocked = !zoffsets && layer < 0 ? p->umajor : 0;  // the layout of dense-product plans
     std::vector<double> z(L + 1, 0.0);
     for (int l = 0; l < L; ++l) z[l + 1] = z[l] + p->thickness[l];
 
@@ -216,6 +217,11 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
             rc = cuda_fail(e, "cudaMemcpyAsync(tensor set-up)");
             break;
         }
+        // the blocked layout writes only the layers that exist: zero the rest
+        if (blocked && (e = cudaMemsetAsync(dst, 0, p->tensor_bytes, st)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemsetAsync(tensor)");
+            break;
+        }
         for (int p0 = 0; p0 < npairs && rc == DEMAG_OK; p0 += chunk) {
             const int np = std::min(chunk, npairs - p0);
             if ((e = cudaMemsetAsync(planes, 0, plane_bytes * np, st)) != cudaSuccess) {
@@ -238,9 +244,8 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
             }
             if ((e = launch_extract_tensor(planes, f32, p0, np, npairs, p->log2Px, p->log2Py,
                                            zoffsets ? tensor_row(p->log2Py, true) : p->QyS, dst,
-                                           zoffsets || p->precision == DEMAG_PREC_FP64, st,
-                                           zoffsets ? 0 : (layer < 0 ? p->umajor : 0),
-                                           zoffsets ? 1 : p->natural)) != cudaSuccess) {
+                                           zoffsets || p->precision == DEMAG_PREC_FP64, st, blocked,
+                                           zoffsets ? 1 : p->natural, d_pi, d_pj, d_th, L)) != cudaSuccess) {
                 rc = cuda_fail(e, "tensor extraction kernel");
                 break;
             }
@@ -440,7 +445,7 @@ static demag_status plan_create_impl(demag_plan_t *plan, int nx, int ny, double 
     const size_t real = fp64 ? sizeof(double) : sizeof(float);
     const size_t cpx = 2 * real;
     p->tensor_bytes = p->method == 1 ? (size_t)p->Kx * p->Qy * ((1 << p->log2Pz) / 2 + 1) * 6 * real
-                      : p->umajor    ? (size_t)p->Kx * p->Qy * umajor_block(p->npairs) * real
+                      : p->umajor    ? (size_t)p->Kx * p->Qy * ub_entry(L) * real
                                      : (size_t)p->Kx * p->npairs * 6 * p->QyS * real;
     p->field_bytes_per_state = (size_t)L * 3 * ny * nx * real;
     if (rc == DEMAG_OK) rc = dalloc(&p->d_tensor, p->tensor_bytes, "tensor");

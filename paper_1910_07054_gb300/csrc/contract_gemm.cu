@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
     // compact tensor
     for (int e = threadIdx.x; e < 6 * Lp * S + 2 * 6 * Bp * S; e += kGemmThreads) smem_f[e] = 0.f;
     __syncthreads();
-    // compact tensor of the entry: npairs * 6 floats, contiguous and 16-byte
+    // compact tensor of the entry (blocked, layout.cuh), contiguous and 16-byte
     // aligned; all loads of a thread are issued before any is used
-    const int NB = umajor_block(npairs), NR = umajor_row(npairs);
+    const int nb = ub_nb(L), NR = ub_row(L), NB = 6 * NR;
     const float4 *tu4 = reinterpret_cast<const float4 *>(tensor_um + ((size_t)kx * Qy + u) * NB);
     const int n4 = NB / 4;
     constexpr int kBatch = 8;
@@ -119,21 +119,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int e = 4 * e4 + w;
-                const int c = e / NR, P = e - c * NR;  // [component][pair] rows of NR
-                if (P >= npairs) continue;             // row padding
-                // pair P = (a, b), a <= b, numbered row by row: invert the
-                // triangular count from the end, r = T - 1 - P
-                const int T = L * (L + 1) / 2, r = T - 1 - P;
-                int kk = (int)((sqrtf(8.f * (float)r + 1.f) - 1.f) * 0.5f);
-                while ((kk + 1) * (kk + 2) / 2 <= r) ++kk;
-                while (kk * (kk + 1) / 2 > r) --kk;
-                const int a = L - 1 - kk;
-                const int b = L - 1 - (r - kk * (kk + 1) / 2);
-                Kd[(c * Lp + a) * S + b] = vals[w];  // target a <- source b
-                if (b != a) {
-                    const float rr = ratio[b * L + a] * (c >= 4 ? -1.f : 1.f);  // target b <- source a
-                    Kd[(c * Lp + b) * S + a] = rr * vals[w];
+                const int c = e / NR, q = e - c * NR;  // [component][block][row][column]
+                // block (R, C) of index q / 64: block rows of nb, nb - 1, ... blocks
+                int R = 0, rem = q >> 6;
+                while (rem >= nb - R) {
+                    rem -= nb - R;
+                    ++R;
                 }
+                const int a = 8 * R + ((q >> 3) & 7), b = 8 * (R + rem) + (q & 7);
+                if (a >= L || b >= L) continue;  // padding layers
+                // value M(a, b) = (t_a / t_0) N(a <- b): target a <- source b
+                Kd[(c * Lp + a) * S + b] = ratio[a * L] * vals[w];
+                if (rem > 0)  // off-diagonal block: target b <- source a by reciprocity
+                    Kd[(c * Lp + b) * S + a] = ratio[b * L] * (c >= 4 ? -1.f : 1.f) * vals[w];
             }
         }
     }
@@ -282,10 +280,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
 // Tensor-core contraction for B <= 16 (NT = Bp / 8 n-tiles), two blocks per SM.
 //
 // The compact tensor of the entry stays compact in shared memory: each
-// m16n8k8 A fragment element (target i, source j) is read from the stored
-// pair (min, max) and, for i > j, scaled by t_j / t_i = tau_j / tau_i
-// (tau_l = t_l / t_0) with xz and yz negated (reciprocity), so the six dense
-// L x L matrices are never formed.  Warp unit = (m-tile of 16 targets,
+// m16n8k8 A fragment element (target i, source j) is M(i, j) t_0 / t_i, with
+// M(i, j) read from its 8 x 8 block (layout.cuh), or for a block below the
+// diagonal from element (j, i) of the transposed block with xz and yz negated
+// (reciprocity), so the six dense L x L matrices are never formed.  Warp unit = (m-tile of 16 targets,
 // position); it keeps the six outputs of its unit in registers and, per
 // k-step, splits the 6 x NT state fragments once and each component's A
 // fragment once, then issues the 18 products (3 TF32 passes each).
@@ -296,7 +294,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_contract_tc(float2 *__restr
                                                                int log2Py, int npairs) {
     extern __shared__ __align__(16) float smem_f[];
     const int Lp = pad16(L), Bp = 8 * NT, S = gemm_stride(Lp);
-    const int NB = umajor_block(npairs), NR = umajor_row(npairs);
+    const int nb = ub_nb(L), NR = ub_row(L), NB = 6 * NR;
     float *raw = smem_f;                     // [6][NR]: the entry's component rows
     float *Ms = smem_f + NB;                 // [2][6][Bp][S]: M_s[b][j]; later the output rows
     float *s_tau = Ms + 2 * 6 * Bp * S;      // [Lp]: t_l / t_0
@@ -399,10 +397,12 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_contract_tc(float2 *__restr
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 const int i = mt * 16 + gr + ((f & 1) ? 8 : 0), jj = k0 + gc + ((f & 2) ? 4 : 0);
-                const int lo = i < jj ? i : jj, hi = i < jj ? jj : i;
-                base[f] = (i < L && jj < L) ? (lo * L - (lo * (lo - 1)) / 2 + (hi - lo)) : -1;
-                rev[f] = i > jj;
-                scl[f] = rev[f] ? s_tau[jj] * s_itau[i] : 1.f;
+                const int I = i >> 3, J = jj >> 3;
+                rev[f] = I > J;
+                base[f] = (i < L && jj < L) ? (rev[f] ? ub_blk(J, I, nb) + 8 * (jj & 7) + (i & 7)
+                                                      : ub_blk(I, J, nb) + 8 * (i & 7) + (jj & 7))
+                                            : -1;
+                scl[f] = s_itau[i];
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_contract_tc(float2 *__restr
 
 size_t tc_smem_bytes(int L, int npairs) {
     const int Lp = pad16(L), S = gemm_stride(Lp);
-    return (size_t)(umajor_block(npairs) + 2 * 6 * 16 * S + 2 * Lp) * sizeof(float);
+    return (size_t)(ub_entry(L) + 2 * 6 * 16 * S + 2 * Lp) * sizeof(float);
 }
 
 }  // namespace demag

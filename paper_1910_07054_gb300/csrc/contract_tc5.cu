@@ -15,9 +15,13 @@
 // so that rows x and y of D are (Re H, Im H) and rows z are (Im H_z, -Re H_z).
 // A is that of the stored frequency for both positions: at the mirrored one
 // (where xy and yz change sign) m_y enters S negated and H_y leaves D negated.
-// K_c(i <- j) is the stored pair (i <= j), or for i > j the stored (j, i)
-// times t_j / t_i with xz and yz negated (reciprocity).  Products: a = a_hi +
-// a_lo, s = s_hi + s_lo (TF32), D += a_lo s_hi + a_hi s_lo + a_hi s_hi in FP32.
+// The kernel builds A with its rows prescaled by t_i / t_0, from the stored
+// blocks of M(i, j) = (t_i / t_0) K(i <- j) (layout.cuh): a row of a block on
+// or above the diagonal is 8 consecutive values, and below the diagonal M(i, j)
+// = s_c M(j, i) is a column of the transposed block (s_c = -1 for xz and yz:
+// reciprocity), so no value needs a per-element scale or selection; the
+// epilogue multiplies row i of D by t_0 / t_i.  Products: a = a_hi + a_lo,
+// s = s_hi + s_lo, D += a_lo s_hi + a_hi s_lo + a_hi s_hi in FP32.
 //
 // One persistent block per SM walks the entries.  A lives in tensor memory:
 // each producer thread builds its own row of A (the thread's TMEM lane) for
@@ -28,14 +32,15 @@
 //                state rows (one copy per state, to a bank-spreading stride)
 //                into one of two input buffers, and L2 prefetch two entries
 //                ahead;
-//   warps 0-15   producers, chunk by chunk of 16 columns of K, 3 stages: a warp
-//                of lane quarter q (warp mod 4) builds hi and lo of the A rows in
-//                TMEM lanes 32 q + lane of one 128-row tile t, K columns
-//                8 h..8 h + 7, for one (t, h); warps without such a block build S
-//                (hi and lo, K-major canonical layout) in shared memory;
+//   warps 0-15   producers, chunk by chunk of K (16 TF32 or 32 BF16 columns),
+//                2 stages: a warp of lane quarter q (warp mod 4) builds hi and
+//                lo of the A rows in TMEM lanes 32 q + lane of one 128-row tile
+//                t, its half h of the chunk's K columns, for one (t, h); warps
+//                without such a block build S (hi and lo, K-major canonical
+//                layout) in shared memory;
 //   warp 20      MMA issue (one thread; M = 128 row tiles, N = 64) and the
 //                tensor-memory allocation (512 columns: accumulators
-//                double-buffered in 0..255, the A stages in 256..511);
+//                double-buffered in 0..255, the A stages from 256);
 //   warps 16-19  epilogue: accumulators to the state rows.
 // Row r < 128 of A and D is lane r of tile 0; rows 128..3 Lp - 1 are the top
 // lanes of tile 1 (lane r - 128 + lane0 of tile 1, lane0 a multiple of 32), so
@@ -62,7 +67,7 @@ constexpr int kTcBp = 16;
 // K columns per chunk (two MMA k-steps): 16 TF32 or 32 BF16 values, 64 bytes
 // of each S row either way
 template <bool BF> struct TcKC { static constexpr int value = BF ? 32 : 16; };
-constexpr int kTcStages = 3;
+constexpr int kTcStages = 2;
 constexpr int kTcCols = 512;     // tensor memory allocated
 constexpr int kTcAcol = 256;     // first column of the A stages
 constexpr int kTcAstage = 64;    // columns per A stage: 2 tiles x (16 hi + 16 lo)
@@ -85,7 +90,7 @@ __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs, int kc = 1
     s.R = 3 * s.Lp;
     s.T = (s.R + 127) / 128;
     s.nch = (s.R + kc - 1) / kc;  // K = R padded to whole chunks (zero columns)
-    s.NB = umajor_block(npairs);
+    s.NB = ub_entry(L);
     // a state's 3L complex values, padded so that consecutive states start 16
     // bytes apart modulo 128 (the 8 states a warp reads at once hit 8 bank groups)
     s.seg = 3 * L + ((2 - (3 * L) % 16) + 16) % 16;
@@ -120,20 +125,6 @@ __device__ __forceinline__ void split_tf32(float v, uint32_t &hi, uint32_t &lo) 
     lo = __float_as_uint(v - __uint_as_float(hi));
 }
 
-// Round a finite float to BF16 (8 significant bits), to nearest with ties to
-// even, as the upper 16 bits of a float.
-__device__ __forceinline__ uint32_t bf16_round(uint32_t bits) {
-    return (bits + 0x7FFFu + ((bits >> 16) & 1u)) & 0xFFFF0000u;
-}
-
-// v = hi + lo + r with hi = bf16(v), lo = bf16(v - hi) (|r| <= 2^-18 |v|);
-// returned as the two 16-bit patterns.
-__device__ __forceinline__ void split_bf16(float v, uint32_t &hi, uint32_t &lo) {
-    const uint32_t h = bf16_round(__float_as_uint(v));
-    hi = h >> 16;
-    lo = bf16_round(__float_as_uint(v - __uint_as_float(h))) >> 16;
-}
-
 // Split of one 32-bit operand word: TF32 takes one value per word, BF16 two
 // (the lower K index in the low half).
 template <bool BF> struct Split;
@@ -145,9 +136,9 @@ template <> struct Split<false> {
 };
 template <> struct Split<true> {
     static constexpr int kPerWord = 2;
-    // the same rounding as split_bf16, two values at a time with the
-    // hardware's paired conversion (round to nearest even): six instructions
-    // for the pair
+    // v = hi + lo + r with hi = bf16(v), lo = bf16(v - hi), both rounded to
+    // nearest even (|r| <= 2^-18 |v|), two values at a time with the
+    // hardware's paired conversion: six instructions for the pair
     __device__ __forceinline__ static void word(const float *v, uint32_t &hi, uint32_t &lo) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);  // .x (low half) = v[0]
         const uint32_t hb = *reinterpret_cast<const uint32_t *>(&h);
@@ -200,8 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
     __shared__ __align__(8) uint64_t st_full[kTcStages], st_empty[kTcStages], d_full[2], d_empty[2];
     __shared__ __align__(8) uint64_t in_full[2], in_empty[2];  // the entry's tensor and state rows
     __shared__ unsigned tmem_slot;
-    __shared__ __align__(16) float s_tau[64], s_itau[64];
-    __shared__ __align__(16) int s_rb[64];  // index of pair (i, i) minus i: pair (i, j >= i) is s_rb[i] + j
+    __shared__ __align__(16) float s_itau[64];
     __shared__ int s_abort;
     constexpr int KC = TcKC<BF>::value;  // K columns per chunk
     constexpr int PW = Split<BF>::kPerWord;
@@ -227,11 +217,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         mbar_init_fence();
         s_abort = 0;
     }
-    if (tid < 64) {
-        s_tau[tid] = tid < L ? ratio[tid] : 0.f;       // t_l / t_0
-        s_itau[tid] = tid < L ? ratio[tid * L] : 0.f;  // t_0 / t_l
-        s_rb[tid] = tid * L - (tid * (tid - 1)) / 2 - tid;
-    }
+    if (tid < 64) s_itau[tid] = tid < L ? ratio[tid * L] : 0.f;  // t_0 / t_l
     if (warp == kTcMma) tc_alloc(&tmem_slot, kTcCols);
     tc_fence_before();
     __syncthreads();
@@ -318,33 +304,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
             if (s_w && w < warp) ++sidx;
             nS += s_w;
         }
-        const int NR = umajor_row(npairs);
+        const int nb = ub_nb(L), NR = ub_row(L);
         // All shared-memory operands below are byte offsets from smem (32-bit
         // shared-window addressing).
         // A block: row r of A (co, i), K columns 8 h .. 8 h + 7 of each chunk.
-        // Lanes without a row (r >= 3 Lp or i >= L) read pair (0, j), which
-        // exists, with scale 0.
+        // The row holds M(i, j) (the layer matrix prescaled by t_i / t_0; the
+        // epilogue takes t_0 / t_i back out).  Lanes without a row (r >= 3 Lp)
+        // read row 0 of component 0: finite values for accumulator rows that
+        // are never read; rows L <= i < Lp read the zero padding.
         const int t = (wq >> 1) > 0 || 32 * q >= R, h = wq & 1;  // a quarter without tile-0 rows has tile 1 only
         const int r = t == 0 ? 32 * q + lane : 128 + 32 * q + lane - lane0;
         const int cor = r / Lp;
-        const bool rvalid = isA && r < R && r - cor * Lp < L;
-        const int co = rvalid ? cor : 0, i = rvalid ? r - cor * Lp : 0;
-        const float vs = rvalid ? 1.f : 0.f;
-        const int srb_i = s_rb[i];
-        const float itau_i = s_itau[i];
+        const bool rin = isA && r < R;
+        const int co = rin ? cor : 0, i = rin ? r - cor * Lp : 0;
+        const int I = i >> 3, i8 = i & 7;  // the row's block row and its row in the block
         const unsigned ta_row = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(kTcAcol + 32 * t + 8 * h);
         // per source component ci: byte offset of the stored component row, and
-        // the scale of the upper (j >= i, stored pair (i, j)) and lower (j < i,
-        // stored pair (j, i) times t_j / t_i, xz and yz negated) triangles
+        // the sign of blocks on or above the diagonal (-1 for the -K_zz block of
+        // A) and below it (there xz and yz also change sign: reciprocity)
         int offc[3];
         float sup[3], slo[3];
 #pragma unroll
         for (int ci = 0; ci < 3; ++ci) {
             const int comp = tc_comp(co, ci);
-            const float zs = (co == 2 && ci == 2) ? -vs : vs;
+            const float zs = (co == 2 && ci == 2) ? -1.f : 1.f;
             offc[ci] = comp * NR * 4;
             sup[ci] = zs;
-            slo[ci] = zs * itau_i * (comp >= 4 ? -1.f : 1.f);
+            slo[ci] = comp >= 4 ? -zs : zs;
         }
         // S unit of this thread: (position pq, state b, core column k4)
         constexpr int KG = 4;  // core matrices (16 bytes of K) per S row and chunk
@@ -379,36 +365,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                         const int kc0 = ch * KC + 8 * PW * h + 8 * sbk;  // first K column of the sub-block
                         float *vs8 = v + 8 * sbk;
                         if (kc0 < R) {
-                            const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), jb = kc0 - ci * Lp;
+                            // the sub-block is layer block J of source component ci
+                            const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), J = (kc0 - ci * Lp) >> 3;
                             const int off = inb + (ci == 0 ? offc[0] : (ci == 1 ? offc[1] : offc[2]));
-                            const float su = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
-                            const float sl = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
-                            const int bu = off + (srb_i + jb) * 4;  // + 4 e: pair (i, jb + e)
-                            const int bl = off + i * 4;             // + 4 s_rb[j]: pair (j, i)
-                            const int4 rb0 = *reinterpret_cast<const int4 *>(s_rb + jb);
-                            const int4 rb1 = *reinterpret_cast<const int4 *>(s_rb + jb + 4);
-                            const float4 tj0 = *reinterpret_cast<const float4 *>(s_tau + jb);
-                            const float4 tj1 = *reinterpret_cast<const float4 *>(s_tau + jb + 4);
-                            const int rbj[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
-                            const float tj[8] = {tj0.x, tj0.y, tj0.z, tj0.w, tj1.x, tj1.y, tj1.z, tj1.w};
-                            const int d = i - jb;  // column e is in the upper triangle iff e >= d
-                            if (jb + 8 <= L) {
-#pragma unroll
-                                for (int e = 0; e < 8; ++e) {
-                                    const bool up = e >= d;
-                                    const int a = up ? bu + 4 * e : bl + 4 * rbj[e];
-                                    const float sc = up ? su : sl * tj[e];
-                                    vs8[e] = sc * *reinterpret_cast<const float *>(smem + a);
-                                }
+                            float sg;
+                            if (I <= J) {
+                                // row i8 of block (I, J): 8 consecutive values
+                                const float4 *src =
+                                    reinterpret_cast<const float4 *>(smem + off + 4 * (ub_blk(I, J, nb) + 8 * i8));
+                                const float4 x0 = src[0], x1 = src[1];
+                                vs8[0] = x0.x, vs8[1] = x0.y, vs8[2] = x0.z, vs8[3] = x0.w;
+                                vs8[4] = x1.x, vs8[5] = x1.y, vs8[6] = x1.z, vs8[7] = x1.w;
+                                sg = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
                             } else {
-                                // last block of a component: columns j >= L are zero
+                                // column i8 of block (J, I): M(i, 8 J + e) = s_c M(8 J + e, i)
+                                const float *src =
+                                    reinterpret_cast<const float *>(smem + off + 4 * (ub_blk(J, I, nb) + i8));
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) {
-                                    const bool in = jb + e < L, up = e >= d;
-                                    const int a = !in ? off : (up ? bu + 4 * e : bl + 4 * rbj[e]);
-                                    const float sc = !in ? 0.f : (up ? su : sl * tj[e]);
-                                    vs8[e] = sc * *reinterpret_cast<const float *>(smem + a);
-                                }
+                                for (int e = 0; e < 8; ++e) vs8[e] = src[8 * e];
+                                sg = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2) {
+                                const float2 y = __fmul2_rn(make_float2(vs8[e], vs8[e + 1]), make_float2(sg, sg));
+                                vs8[e] = y.x;
+                                vs8[e + 1] = y.y;
                             }
                         } else {
 #pragma unroll
@@ -534,11 +515,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                     }
                     if (!lane_row || pq >= npos || rg >= R || ig >= L) continue;
                     const bool mir = (pq == 0) == mir0;
+                    const float rs = s_itau[ig];  // the rows of A were prescaled by t_i / t_0
                     float2 *dst = spec2 + ((size_t)kx * Py + (pq ? p2 : p1)) * planes + ig * 3 + cog;
 #pragma unroll
                     for (int b = 0; b < kTcBp; ++b) {
                         if (b >= B) break;
-                        const float dre = __uint_as_float(rr[b]), dim = __uint_as_float(rr[16 + b]);
+                        const float dre = rs * __uint_as_float(rr[b]), dim = rs * __uint_as_float(rr[16 + b]);
                         float2 hh;
                         if (cog == 2)
                             hh = make_float2(-dim, dre);

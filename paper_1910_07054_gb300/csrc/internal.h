@@ -62,9 +62,13 @@ cudaError_t launch_fft2_planes(void *planes, bool f32, int nplanes, int log2Px, 
 // the plan tensor, scaled by 1/(Px Py), y-frequencies in the stored order of
 // layout.cuh: [Kx][npairs][6][QyS] (umajor = 0) or [Kx][Qy][npairs][6]
 // (umajor = 1, float only).
+// umajor: the blocked layout of dense-product plans (layout.cuh), which needs
+// the pair lists (target i <= source j), the thicknesses and L.
 cudaError_t launch_extract_tensor(const void *planes, bool f32, int p0, int np, int npairs,
                                   int log2Px, int log2Py, int QyS, void *tensor, bool fp64,
-                                  cudaStream_t st, int umajor = 0, int natural = 0);
+                                  cudaStream_t st, int umajor = 0, int natural = 0,
+                                  const int *pair_i = nullptr, const int *pair_j = nullptr,
+                                  const double *th = nullptr, int L = 0);
 
 // ---- apply ---------------------------------------------------------------
 struct ApplyArgs {

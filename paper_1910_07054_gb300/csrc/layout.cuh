@@ -56,11 +56,21 @@ __host__ __device__ inline int tensor_row(int log2Py, bool fp64) {
     return (Qy + q - 1) / q * q;
 }
 
-// The u-major tensor layout (dense-product plans) holds one (kx, u) block of
-// 6 component rows, [component][pair]; each row is npairs padded to a multiple
-// of 4, so rows and blocks start on 16-byte boundaries.
-__host__ __device__ inline int umajor_row(int npairs) { return (npairs + 3) / 4 * 4; }
-// Floats per (kx, u) block.
-__host__ __device__ inline int umajor_block(int npairs) { return 6 * umajor_row(npairs); }
+// The u-major tensor layout (dense-product plans) holds one (kx, u) entry of
+// 6 component rows.  A component row holds the layer matrix prescaled by the
+// target thickness, M(i, j) = (t_i / t_0) N(i <- j), in 8 x 8 blocks of layers
+// (R, C), R <= C, block row by block row, each block row-major (row i, column
+// j).  Off-diagonal blocks hold pairs i < j; a diagonal block holds both
+// triangles, the lower one as M(i, j) = s_c M(j, i) with s_c = -1 for xz and
+// yz, +1 otherwise (reciprocity, t_i N(i <- j) = t_j P N(j <- i) P with P =
+// diag(1, 1, -1)).  Layers past L are zero.  For i > j in different blocks
+// M(i, j) is s_c times element (j, i) of block (C, R).
+__host__ __device__ inline int ub_nb(int L) { return (L + 7) / 8; }
+// Floats per component row (a multiple of 64, so rows and blocks start on
+// 256-byte boundaries) and per (kx, u) entry.
+__host__ __device__ inline int ub_row(int L) { return ub_nb(L) * (ub_nb(L) + 1) / 2 * 64; }
+__host__ __device__ inline int ub_entry(int L) { return 6 * ub_row(L); }
+// First float of block (R, C), R <= C, in a component row.
+__host__ __device__ inline int ub_blk(int R, int C, int nb) { return (R * nb - R * (R - 1) / 2 + (C - R)) * 64; }
 
 }  // namespace demag

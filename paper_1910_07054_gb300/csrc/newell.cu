@@ -792,9 +792,9 @@ __global__ void __launch_bounds__(32) k_near_planes(C *__restrict__ planes, int 
     double N[6];
 #pragma unroll 1
     for (int c = 0; c < 6; ++c) {
-        const int A = kAx[c][0], Bx = kAx[c][1], C = kAx[c][2];
-        const double X = o[A], Y = o[Bx], Z = o[C];
-        const double TX = t[A], TY = t[Bx], TZ = t[C], SX = s[A], SY = s[Bx], SZ = s[C];
+        const int A = kAx[c][0], Bx = kAx[c][1], Cz = kAx[c][2];
+        const double X = o[A], Y = o[Bx], Z = o[Cz];
+        const double TX = t[A], TY = t[Bx], TZ = t[Cz], SX = s[A], SY = s[Bx], SZ = s[Cz];
         double acc = 0.0;
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -1039,11 +1039,15 @@ cudaError_t launch_fft2_planes(void *planes, bool f32, int nplanes, int log2Px, 
 // stored entry u holding ky = u_kyq(u) (layout.cuh).
 // plane 0 = FFT(N_xx) + i FFT(N_yy), both real; plane 1 = FFT(N_zz) + i FFT(N_xy),
 // both real; plane 2 = FFT(N_xz) + i FFT(N_yz) = i a - b with FFT(N_xz) = i a,
-// FFT(N_yz) = i b.
+// FFT(N_yz) = i b.  Dense-product plans (umajor) write the blocked, prescaled
+// layout of layout.cuh: pair (i, j) of the pair lists, times t_i / t_0, and in
+// a diagonal block also its mirror (j, i) with xz and yz negated; the tensor
+// is zeroed beforehand (padding layers).
 template <typename T, typename C>
 __global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npairs,
                           int log2Px, int log2Py, int QyS, T *__restrict__ tensor, int umajor,
-                          int natural) {
+                          int natural, const int *__restrict__ pair_i, const int *__restrict__ pair_j,
+                          const double *__restrict__ th, int L) {
     const int Px = 1 << log2Px, Py = 1 << log2Py;
     const int Kx = Px / 2 + 1, Qy = Py / 2 + 1;
     const long long total = (long long)np * Kx * Qy;
@@ -1058,9 +1062,22 @@ __global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npai
     const double2 Bp = make_double2(base[(size_t)Px * Py].x, base[(size_t)Px * Py].y);
     const double2 Cc = make_double2(base[(size_t)2 * Px * Py].x, base[(size_t)2 * Px * Py].y);
     const double sc = 1.0 / ((double)Px * (double)Py);
-    const size_t cs = umajor ? (size_t)umajor_row(npairs) : QyS;  // component stride
-    T *o = umajor ? tensor + ((size_t)kx * Qy + u) * umajor_block(npairs) + (size_t)(p0 + P)
-                  : tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * QyS + u;
+    if (umajor) {
+        const int i = pair_i[p0 + P], j = pair_j[p0 + P], nb = ub_nb(L), rl = ub_row(L);
+        const double f = sc * th[i] / th[0];
+        const double v[6] = {A.x * f, A.y * f, Bp.x * f, Bp.y * f, Cc.y * f, -Cc.x * f};
+        T *o = tensor + ((size_t)kx * Qy + u) * (6 * (size_t)rl);
+        const int I = i >> 3, J = j >> 3;
+        const int e1 = ub_blk(I, J, nb) + 8 * (i & 7) + (j & 7);
+        for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e1] = (T)v[c];
+        if (I == J && i != j) {
+            const int e2 = ub_blk(I, I, nb) + 8 * (j & 7) + (i & 7);
+            for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e2] = (T)(c >= 4 ? -v[c] : v[c]);
+        }
+        return;
+    }
+    const size_t cs = QyS;  // component stride
+    T *o = tensor + ((size_t)kx * npairs + (p0 + P)) * 6 * QyS + u;
     o[0 * cs] = (T)(A.x * sc);
     o[1 * cs] = (T)(A.y * sc);
     o[2 * cs] = (T)(Bp.x * sc);
@@ -1071,23 +1088,29 @@ __global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npai
 
 cudaError_t launch_extract_tensor(const void *planes, bool f32, int p0, int np, int npairs, int log2Px,
                                   int log2Py, int QyS, void *tensor, bool fp64, cudaStream_t st,
-                                  int umajor, int natural) {
+                                  int umajor, int natural, const int *pair_i, const int *pair_j,
+                                  const double *th, int L) {
+    if (umajor && (fp64 || !pair_i || !pair_j || !th || L < 1)) return cudaErrorInvalidValue;
     const long long total = (long long)np * ((1 << log2Px) / 2 + 1) * ((1 << log2Py) / 2 + 1);
     const unsigned grid = (unsigned)((total + 255) / 256);
     if (f32) {
         if (fp64)
             k_extract<double, float2><<<grid, 256, 0, st>>>((const float2 *)planes, p0, np, npairs, log2Px, log2Py,
-                                                            QyS, (double *)tensor, umajor, natural);
+                                                            QyS, (double *)tensor, umajor, natural, pair_i,
+                                                            pair_j, th, L);
         else
             k_extract<float, float2><<<grid, 256, 0, st>>>((const float2 *)planes, p0, np, npairs, log2Px, log2Py,
-                                                           QyS, (float *)tensor, umajor, natural);
+                                                           QyS, (float *)tensor, umajor, natural, pair_i,
+                                                           pair_j, th, L);
     } else {
         if (fp64)
             k_extract<double, double2><<<grid, 256, 0, st>>>((const double2 *)planes, p0, np, npairs, log2Px,
-                                                             log2Py, QyS, (double *)tensor, umajor, natural);
+                                                             log2Py, QyS, (double *)tensor, umajor, natural,
+                                                             pair_i, pair_j, th, L);
         else
             k_extract<float, double2><<<grid, 256, 0, st>>>((const double2 *)planes, p0, np, npairs, log2Px,
-                                                            log2Py, QyS, (float *)tensor, umajor, natural);
+                                                            log2Py, QyS, (float *)tensor, umajor, natural,
+                                                            pair_i, pair_j, th, L);
     }
     return cudaGetLastError();
 }
