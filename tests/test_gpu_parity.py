@@ -313,3 +313,53 @@ def test_gpu_argument_errors():
     with pytest.raises(TypeError):
         plan.apply(m1.double(), 1.0)
     plan.close()
+
+
+@pytest.mark.parametrize("nx,ny,th", [(7, 5, (1.0, 0.5, 2.0)),
+                                      (9, 6, tuple(np.round(np.linspace(0.6, 2.4, 10), 3)))])
+def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
+    """A dense-product plan's stored tensor, decoded here from the documented
+    blocked layout (8 x 8 layer blocks R <= C of M(i, j) = (t_i / t_0) N(i <- j),
+    diagonal blocks mirrored with xz and yz negated, layers past L zero), equals
+    the oracle's transformed kernels.  10 layers cross a block boundary."""
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=1)
+    info = plan.info
+    Px, Py, L = info["Px"], info["Py"], info["L"]
+    Kx, Qy = Px // 2 + 1, Py // 2 + 1
+    nb = (L + 7) // 8
+    row = 64 * nb * (nb + 1) // 2
+    out = torch.empty(Kx * Qy * 6 * row, dtype=torch.float32, device="cuda")
+    dm.demag_plan_tensor(plan.handle, out)
+    torch.cuda.synchronize()
+    T = out.cpu().numpy().astype(np.float64).reshape(Kx, Qy, 6, row)
+    plan.close()
+    ky_of_u = _stored_ky(Py, info["path"])
+    K = reading_kernels(nx, ny, 2.0, 2.0, tuple(th))
+    qs = np.arange(-(ny - 1), ny) % Py
+    ps = np.arange(-(nx - 1), nx) % Px
+    ref = {}
+    for i in range(L):
+        for j in range(i, L):
+            Kp = np.zeros((6, Py, Px))
+            Kp[:, qs[:, None], ps[None, :]] = K[i, j]
+            S = np.fft.fft2(Kp) / (Px * Py)
+            R = np.stack([S[0].real, S[1].real, S[2].real, S[3].real, S[4].imag, S[5].imag])
+            ref[i, j] = np.transpose(R[:, ky_of_u, :Kx], (2, 1, 0))  # [kx, u, component]
+    sign = np.array([1.0, 1.0, 1.0, 1.0, -1.0, -1.0])
+    exp = np.zeros_like(T)
+    blk = 0
+    for Rb in range(nb):
+        for Cb in range(Rb, nb):
+            for a in range(8):
+                for b in range(8):
+                    i, j = 8 * Rb + a, 8 * Cb + b
+                    if i >= L or j >= L:
+                        continue
+                    e = 64 * blk + 8 * a + b
+                    if i <= j:
+                        exp[:, :, :, e] = th[i] / th[0] * ref[i, j]
+                    else:  # lower half of a diagonal block
+                        exp[:, :, :, e] = sign * th[j] / th[0] * ref[j, i]
+            blk += 1
+    sc = np.abs(exp).max()
+    assert np.abs(T - exp).max() < 2e-6 * sc
