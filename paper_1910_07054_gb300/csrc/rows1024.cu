@@ -57,8 +57,25 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_rows_forward1024(const float
         b[bs.bj + 68 * r] = v[1][r];  // Z[2k + 1]
     }
     __syncthreads();
-    // untangle and store transposed: lane (kx, row r of the block)
     float2 *sp = spec + (size_t)plane * 513 * ny;
+    if ((ny & 1) == 0) {
+        // untangle and store transposed, one item per (kx, row pair q): rows a
+        // and b of the pair are adjacent in the spectrum, so both leave in one
+        // 16-byte store (ny even) from one pair of reads
+        for (int e = threadIdx.x; e < 513 * kF10Planes; e += kF10Threads) {
+            const int kx = e / kF10Planes, q = e % kF10Planes;
+            const int ya = y0 + 2 * q;
+            if (ya >= ny) continue;
+            const float2 *zp = buf + q * kF10Plane;
+            const int mk = (1024 - kx) & 1023;
+            const float2 z1 = zp[(kx & 1) * kF10Col + f10_pad(kx >> 1)];
+            const float2 z2 = zp[(mk & 1) * kF10Col + f10_pad(mk >> 1)];
+            *reinterpret_cast<float4 *>(sp + (size_t)kx * ny + ya) =
+                make_float4(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y), 0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+        }
+        return;
+    }
+    // odd ny: lane (kx, row r of the block)
     for (int e = threadIdx.x; e < 513 * kR10Rows; e += kF10Threads) {
         const int kx = e >> 4, r = e & (kR10Rows - 1);
         const int y = y0 + r;
@@ -86,36 +103,66 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_rows_inverse1024(const float
     const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
     const float scale = out_scale * (layer_scale ? layer_scale[(plane / 3) % L] : 1.f);
     f10_load_table(tws, tw, sh);
-    // A (even rows of the block) and B (odd rows) of one kx meet in lanes
-    // 2q, 2q + 1; the even lane places Z[kx], the odd one Z[1024 - kx].  The
-    // loops run the same trip count in every thread (whole warps shuffle).
-    // (all 17 loads of a thread are issued before any is placed)
+    // A (even rows of the block) and B (odd rows) of one kx give Z[kx] and
+    // Z[1024 - kx]; all loads of a thread are issued before any is placed.
     const float2 *sp = spec + (size_t)plane * 513 * ny;
-    constexpr int kIt = (513 * kR10Rows + kF10Threads - 1) / kF10Threads;  // 17
-    float2 t[kIt];
+    if ((ny & 1) == 0) {
+        // one item per (kx, row pair q): A and B in one 16-byte load (rows a, b
+        // adjacent, ny even); the item places Z[kx] and Z[1024 - kx]
+        constexpr int kItP = (513 * kF10Planes + kF10Threads - 1) / kF10Threads;  // 9
+        float4 t4[kItP];
 #pragma unroll
-    for (int q = 0; q < kIt; ++q) {
-        const int e = q * kF10Threads + threadIdx.x;
-        const int kx = e >> 4, r = e & (kR10Rows - 1);
-        t[q] = (e < 513 * kR10Rows && y0 + r < ny) ? sp[(size_t)kx * ny + y0 + r] : float2{0.f, 0.f};
-    }
+        for (int q = 0; q < kItP; ++q) {
+            const int e = q * kF10Threads + threadIdx.x;
+            const int kx = e / kF10Planes, ya = y0 + 2 * (e % kF10Planes);
+            t4[q] = (e < 513 * kF10Planes && ya < ny)
+                        ? *reinterpret_cast<const float4 *>(sp + (size_t)kx * ny + ya)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-    for (int q = 0; q < kIt; ++q) {
-        const int e = q * kF10Threads + threadIdx.x;
-        const int kx = e >> 4, r = e & (kR10Rows - 1);
-        const float2 mine = t[q];
-        const float2 other = float2{__shfl_xor_sync(0xffffffffu, mine.x, 1), __shfl_xor_sync(0xffffffffu, mine.y, 1)};
-        if (e >= 513 * kR10Rows) continue;
-        float2 A = (r & 1) ? other : mine, B = (r & 1) ? mine : other;
-        float2 *zp = buf + (r >> 1) * kF10Plane + (kx & 1) * kF10Col;  // 1024 - kx has the parity of kx
-        if (kx == 0 || kx == 512) {
-            A.y = 0.f;
-            B.y = 0.f;
-            if ((r & 1) == 0) zp[f10_pad(kx >> 1)] = float2{A.x, B.x};
-        } else if ((r & 1) == 0) {
-            zp[f10_pad(kx >> 1)] = float2{A.x - B.y, A.y + B.x};
-        } else {
-            zp[f10_pad((1024 - kx) >> 1)] = float2{A.x + B.y, B.x - A.y};
+        for (int q = 0; q < kItP; ++q) {
+            const int e = q * kF10Threads + threadIdx.x;
+            if (e >= 513 * kF10Planes) continue;
+            const int kx = e / kF10Planes, pq = e % kF10Planes;
+            const float2 A = make_float2(t4[q].x, t4[q].y), B = make_float2(t4[q].z, t4[q].w);
+            float2 *zp = buf + pq * kF10Plane + (kx & 1) * kF10Col;  // 1024 - kx has the parity of kx
+            if (kx == 0 || kx == 512) {
+                zp[f10_pad(kx >> 1)] = float2{A.x, B.x};  // A, B real at DC and Nyquist
+            } else {
+                zp[f10_pad(kx >> 1)] = float2{A.x - B.y, A.y + B.x};
+                zp[f10_pad((1024 - kx) >> 1)] = float2{A.x + B.y, B.x - A.y};
+            }
+        }
+    } else {
+        // odd ny: one item per (kx, row r); A and B meet in lanes 2q, 2q + 1, the
+        // even lane places Z[kx], the odd one Z[1024 - kx] (the loops run the
+        // same trip count in every thread: whole warps shuffle)
+        constexpr int kIt = (513 * kR10Rows + kF10Threads - 1) / kF10Threads;  // 17
+        float2 t[kIt];
+#pragma unroll
+        for (int q = 0; q < kIt; ++q) {
+            const int e = q * kF10Threads + threadIdx.x;
+            const int kx = e >> 4, r = e & (kR10Rows - 1);
+            t[q] = (e < 513 * kR10Rows && y0 + r < ny) ? sp[(size_t)kx * ny + y0 + r] : float2{0.f, 0.f};
+        }
+#pragma unroll
+        for (int q = 0; q < kIt; ++q) {
+            const int e = q * kF10Threads + threadIdx.x;
+            const int kx = e >> 4, r = e & (kR10Rows - 1);
+            const float2 mine = t[q];
+            const float2 other = float2{__shfl_xor_sync(0xffffffffu, mine.x, 1), __shfl_xor_sync(0xffffffffu, mine.y, 1)};
+            if (e >= 513 * kR10Rows) continue;
+            float2 A = (r & 1) ? other : mine, B = (r & 1) ? mine : other;
+            float2 *zp = buf + (r >> 1) * kF10Plane + (kx & 1) * kF10Col;  // 1024 - kx has the parity of kx
+            if (kx == 0 || kx == 512) {
+                A.y = 0.f;
+                B.y = 0.f;
+                if ((r & 1) == 0) zp[f10_pad(kx >> 1)] = float2{A.x, B.x};
+            } else if ((r & 1) == 0) {
+                zp[f10_pad(kx >> 1)] = float2{A.x - B.y, A.y + B.x};
+            } else {
+                zp[f10_pad((1024 - kx) >> 1)] = float2{A.x + B.y, B.x - A.y};
+            }
         }
     }
     __syncthreads();
