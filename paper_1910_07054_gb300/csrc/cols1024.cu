@@ -72,20 +72,45 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_inverse1024(const fl
     // Y[ky] from row p = bitrev(ky): even frequencies to column a, odd to b
     // (8 loads in flight per thread before their stores)
     const float2 *in = spec2 + (size_t)kx * 1024 * planes + g0;
-    for (int base = 0; base < 1024 * kF10Planes; base += 8 * kF10Threads) {
-        float2 t[8];
+    if ((planes & 1) == 0) {
+        // planes in pairs, one 16-byte load each (planes even: 16-byte aligned);
+        // all 8 loads of a thread in flight before their stores
+        constexpr int kP = kF10Planes / 2;
+        float4 t[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int e = base + q * kF10Threads + threadIdx.x;
-            const int ky = e >> 3, gg = e & (kF10Planes - 1);
+            const int e = q * kF10Threads + threadIdx.x;
+            const int ky = e / kP, gg = 2 * (e % kP);
             const int p = (int)(__brev((unsigned)ky) >> 22);
-            t[q] = gg < ng ? in[(size_t)p * planes + gg] : float2{0.f, 0.f};
+            const float2 *src = in + (size_t)p * planes + gg;
+            t[q] = gg + 1 < ng ? *reinterpret_cast<const float4 *>(src)
+                   : gg < ng   ? make_float4(src->x, src->y, 0.f, 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int e = base + q * kF10Threads + threadIdx.x;
-            const int ky = e >> 3, gg = e & (kF10Planes - 1);
-            buf[gg * kF10Plane + (ky & 1) * kF10Col + f10_pad(ky >> 1)] = t[q];
+            const int e = q * kF10Threads + threadIdx.x;
+            const int ky = e / kP, gg = 2 * (e % kP);
+            float2 *dst = buf + gg * kF10Plane + (ky & 1) * kF10Col + f10_pad(ky >> 1);
+            dst[0] = make_float2(t[q].x, t[q].y);
+            dst[kF10Plane] = make_float2(t[q].z, t[q].w);
+        }
+    } else {
+        for (int base = 0; base < 1024 * kF10Planes; base += 8 * kF10Threads) {
+            float2 t[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = base + q * kF10Threads + threadIdx.x;
+                const int ky = e >> 3, gg = e & (kF10Planes - 1);
+                const int p = (int)(__brev((unsigned)ky) >> 22);
+                t[q] = gg < ng ? in[(size_t)p * planes + gg] : float2{0.f, 0.f};
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = base + q * kF10Threads + threadIdx.x;
+                const int ky = e >> 3, gg = e & (kF10Planes - 1);
+                buf[gg * kF10Plane + (ky & 1) * kF10Col + f10_pad(ky >> 1)] = t[q];
+            }
         }
     }
     __syncthreads();
