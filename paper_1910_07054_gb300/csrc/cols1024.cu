@@ -49,6 +49,20 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_forward1024(const fl
     __syncthreads();
     const int ng = min(kF10Planes, planes - g0);
     float2 *out = spec2 + (size_t)kx * 1024 * planes + g0;
+    if ((planes & 1) == 0) {
+        // planes in pairs, one 16-byte store each (planes even: ng is even and
+        // the stores 16-byte aligned)
+        constexpr int kP = kF10Planes / 2;
+        for (int e = threadIdx.x; e < 1024 * kP; e += kF10Threads) {
+            const int ky = e / kP, gg = 2 * (e % kP);
+            if (gg >= ng) continue;
+            const int p = (int)(__brev((unsigned)ky) >> 22);
+            const float2 *src = buf + gg * kF10Plane + (ky & 1) * kF10Col + f10_pad(ky >> 1);
+            const float2 x0 = src[0], x1 = src[kF10Plane];
+            *reinterpret_cast<float4 *>(out + (size_t)p * planes + gg) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < 1024 * kF10Planes; e += kF10Threads) {
         const int ky = e >> 3, gg = e & (kF10Planes - 1);
         if (gg >= ng) continue;

@@ -22,11 +22,12 @@ constexpr int kF10Planes = 8;                 // sequences per block (plane colu
 constexpr int kF10Threads = 64 * kF10Planes;  // one 64-thread group per sequence
 // One padded 512-point column holds index p at p + p / 16 (544 slots); the
 // plane's second column starts 546 slots in (4 words mod 32) and planes are
-// 1092 slots apart (8 words mod 32), so that a warp of the transposed phase
-// (4 consecutive frequencies x 8 planes: a[k], b[k], a[k + 1], b[k + 1] of
-// each plane) needs the minimum two wavefronts.
+// 1094 slots apart (12 words mod 32), so that a warp of the transposed phases
+// that move planes in pairs (8 consecutive frequencies x 4 plane pairs) needs
+// the minimum two wavefronts per access.  The transforms themselves stay
+// within one plane.
 constexpr int kF10Col = 546;
-constexpr int kF10Plane = 2 * kF10Col;
+constexpr int kF10Plane = 2 * kF10Col + 2;
 // Twiddle tables in shared memory: W_1024^k (k < 512), then W_64^m (m < 64),
 // then W_512^j (j < 64) for conflict-free pass-2 and pass-3 lookups.
 constexpr int kF10Tw = 512 + 64 + 64;
