@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_forward1024(const fl
     // positions just read), then out through a transposed store
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        a[bs.bj + 68 * r] = v[0][r];
-        b[bs.bj + 68 * r] = v[1][r];
+        a[bs.bx(r)] = v[0][r];
+        b[bs.bx(r)] = v[1][r];
     }
     __syncthreads();
     const int ng = min(kF10Planes, planes - g0);
@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_inverse1024(const fl
     float2 v[2][8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        v[0][r] = a[bs.bj + 68 * r];
-        v[1][r] = b[bs.bj + 68 * r];
+        v[0][r] = a[bs.bx(r)];
+        v[1][r] = b[bs.bx(r)];
     }
     f10_sync(group);  // pass 1 stores over positions other threads read
     f10_transform<true>(v, a, b, bs, j, group, tws);

@@ -20,20 +20,26 @@ namespace f1024 {
 
 constexpr int kF10Planes = 8;                 // sequences per block (plane columns or row pairs)
 constexpr int kF10Threads = 64 * kF10Planes;  // one 64-thread group per sequence
-// One padded 512-point column holds index p at p + p / 16 (544 slots); the
-// plane's second column starts 546 slots in (4 words mod 32) and planes are
-// 1094 slots apart (12 words mod 32), so that a warp of the transposed phases
-// that move planes in pairs (8 consecutive frequencies x 4 plane pairs) needs
-// the minimum two wavefronts per access.  The transforms themselves stay
-// within one plane.
-constexpr int kF10Col = 546;
+// A padded 512-point column has two layouts.  The exchange layout (the data
+// before pass 1 and after pass 2, and in the transposed phases) holds index p
+// at f10_pad(p) = p + p / 16 + 4 (p / 64) (571 slots); the pass-1 outputs use
+// p + p / 16 (f10_padA).  The extra 4 slots per run of 64 make the pass-2
+// stores (two groups of 8 lanes 64 indices apart in a half-warp) take the
+// minimum two wavefronts, which p + p / 16 alone does not for both the pass-1
+// and pass-2 stores.  The plane's second column starts 574 slots in and planes
+// are 1150 slots apart (28 words mod 32), so that a warp of the transposed
+// phases that move planes in pairs (8 consecutive frequencies x 4 plane pairs)
+// also takes two wavefronts per access.  The transforms themselves stay within
+// one plane.
+constexpr int kF10Col = 574;
 constexpr int kF10Plane = 2 * kF10Col + 2;
 // Twiddle tables in shared memory: W_1024^k (k < 512), then W_64^m (m < 64),
 // then W_512^j (j < 64) for conflict-free pass-2 and pass-3 lookups.
 constexpr int kF10Tw = 512 + 64 + 64;
 constexpr size_t kF10Smem = (size_t)kF10Planes * kF10Plane * sizeof(float2) + kF10Tw * sizeof(float2);
 
-__device__ __forceinline__ int f10_pad(int p) { return p + (p >> 4); }
+__device__ __forceinline__ int f10_pad(int p) { return p + (p >> 4) + 4 * (p >> 6); }
+__device__ __forceinline__ int f10_padA(int p) { return p + (p >> 4); }
 
 __device__ __forceinline__ void f10_sync(int group) {
     asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(64) : "memory");
@@ -54,12 +60,14 @@ __device__ __forceinline__ float2 f10_w(const float2 *tw, int m) {
 
 // Access pattern bases of a thread j (positions of the three Stockham passes
 // in the padded column; see fft8.cuh for the passes):
-//   positions j + 64 r        -> bj + 68 r
-//   pass-1 outputs 8 j + r    -> b1 + r
-//   pass-2 outputs            -> b2 + 8 r + r / 2
+//   positions j + 64 r, pass-1 layout   -> bj + 68 r
+//   positions j + 64 r, exchange layout -> bx(r) = bj + 72 r
+//   pass-1 outputs 8 j + r (pass-1 layout)        -> b1 + r
+//   pass-2 outputs 64 (j / 8) + j mod 8 + 8 r (exchange layout) -> b2 + 8 r + r / 2
 struct F10Bases {
     int bj, b1, b2;
-    __device__ explicit F10Bases(int j) : bj(j + (j >> 4)), b1(8 * j + (j >> 1)), b2(68 * (j >> 3) + (j & 7)) {}
+    __device__ explicit F10Bases(int j) : bj(j + (j >> 4)), b1(8 * j + (j >> 1)), b2(72 * (j >> 3) + (j & 7)) {}
+    __device__ __forceinline__ int bx(int r) const { return bj + 72 * r; }
 };
 
 // Passes 1..3 of both 512-point transforms of a plane; v[0] and v[1] hold the
@@ -106,7 +114,7 @@ __device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, floa
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bj + 68 * r];
+        for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bx(r)];
     {
         // W_512^{rj}: one lookup of W_512^j (consecutive j, no conflict), the
         // other powers by products (within a few ulp of the table values)

@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_rows_forward1024(const float
     f10_transform<false>(v, a, b, bs, j, group, tws);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        a[bs.bj + 68 * r] = v[0][r];  // Z[2k], k = j + 64 r
-        b[bs.bj + 68 * r] = v[1][r];  // Z[2k + 1]
+        a[bs.bx(r)] = v[0][r];  // Z[2k], k = j + 64 r
+        b[bs.bx(r)] = v[1][r];  // Z[2k + 1]
     }
     __syncthreads();
     float2 *sp = spec + (size_t)plane * 513 * ny;
@@ -171,8 +171,8 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_rows_inverse1024(const float
     float2 v[2][8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        v[0][r] = a[bs.bj + 68 * r];
-        v[1][r] = b[bs.bj + 68 * r];
+        v[0][r] = a[bs.bx(r)];
+        v[1][r] = b[bs.bx(r)];
     }
     f10_sync(group);  // pass 1 stores over positions other threads read
     f10_transform<true>(v, a, b, bs, j, group, tws);
