@@ -282,13 +282,15 @@ __global__ void __launch_bounds__(256, 2) k_columns_fused8(typename cpx_of<T>::t
 // the stages drain.  Positions p > 256 take the stored entry q = 512 - p with
 // xy and yz negated, done by negating m_y before and H_y after the sums.
 //
-// Columns are padded by one slot per 16 (index p + p / 16): the stride-1
-// accesses (j + 64 r), the first pass's stride-8 stores (8 j + r) and the
-// second pass's stores (64 (j / 8) + j mod 8 + 8 r) are then all free of bank
-// conflicts for 8-byte elements, with constant offsets from per-thread bases.
+// Columns have two layouts: the pass-1 outputs (stride-8 stores 8 j + r) at
+// p + p / 16 (pad16), everything else (the transforms' inputs and the pass-2
+// outputs, the contraction's positions) at p + p / 16 + 4 (p / 64) (padx16).
+// The stride-1 accesses (j + 64 r), the pass-1 stores and the pass-2 stores
+// (64 (j / 8) + j mod 8 + 8 r) then take the minimum two wavefronts for
+// 8-byte elements, with constant offsets from per-thread bases.
 // The pair loop runs over rows at run time and is unrolled only over the
 // source layer, which keeps the code small enough for the instruction cache.
-constexpr int kColR = kN8 + kN8 / 16;    // padded column length of the streamed kernel
+constexpr int kColR = 572;               // padded column length of the streamed kernel (padx16(511) = 570)
 constexpr int kQyS8 = 260;               // stored frequencies per tensor row (257 padded to 16 B)
 constexpr int kStage8 = 6 * kQyS8;       // floats per pair stage
 constexpr int kRingBudget = 225 * 1024;  // dynamic shared memory of the streamed kernel
@@ -308,6 +310,12 @@ struct Ring8 {
 };
 
 __device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
+// The exchange layout of the row kernels: p + p / 16 + 4 (p / 64).  Their data
+// before pass 1 and after pass 2 (the untangling and placing steps) use it, the
+// pass-1 outputs keep pad16; the 4 extra slots per run of 64 make the pass-2
+// stores (two groups of 8 lanes 64 indices apart in a half-warp) take the
+// minimum two wavefronts.
+__device__ __forceinline__ int padx16(int p) { return p + (p >> 4) + 4 * (p >> 6); }
 
 static __device__ unsigned g_wait_timeouts8;
 
@@ -323,17 +331,20 @@ __device__ __forceinline__ void load_twiddles8(C (&w2)[7], C (&w3)[7], const C *
 }
 
 // Per-thread bases of the three access patterns (see the layout note above).
+// XL (exchange layout, padx16) for the pass-2 stores and pass-3 accesses:
+// j + 64 r -> bj + 72 r, pass-2 store -> b2x + 8 r + r / 2.
 struct Bases8 {
-    int b1;  // 8 j + r       -> b1 + r
-    int bj;  // j + 64 r      -> bj + 68 r
-    int b2;  // pass-2 store  -> b2 + 8 r + r / 2
+    int b1;   // 8 j + r       -> b1 + r
+    int bj;   // j + 64 r      -> bj + 68 r
+    int b2;   // pass-2 store  -> b2 + 8 r + r / 2
+    int b2x;  // the same in the exchange layout
     __device__ explicit Bases8(int j)
-        : b1(8 * j + (j >> 1)), bj(j + (j >> 4)), b2(68 * (j >> 3) + (j & 7)) {}
+        : b1(8 * j + (j >> 1)), bj(j + (j >> 4)), b2(68 * (j >> 3) + (j & 7)), b2x(72 * (j >> 3) + (j & 7)) {}
 };
 
 // Pass 2 of the group's columns c = group + CSTEP u (column stride STRIDE),
 // shared memory to shared memory.
-template <bool INV, int CPG, int STRIDE, int CSTEP, typename C>
+template <bool INV, int CPG, int STRIDE, int CSTEP, typename C, bool XL = false>
 __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const Bases8 &bs, const C (&w2)[7],
                                             C (&v)[CPG][8]) {
 #pragma unroll
@@ -353,7 +364,7 @@ __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const 
 #pragma unroll
             for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w2[r - 1]);
             dft8<INV>(v[u]);
-            C *col = cols + c * STRIDE + bs.b2;
+            C *col = cols + c * STRIDE + (XL ? bs.b2x : bs.b2);
 #pragma unroll
             for (int r = 0; r < 8; ++r) col[8 * r + (r >> 1)] = v[u][r];
         }
@@ -362,22 +373,23 @@ __device__ __forceinline__ void ring8_pass2(C *cols, int group, int ncol, const 
 }
 
 // Pass 3 in place (positions j + 64 r), result left in v.
-template <bool INV, int CPG, int STRIDE, int CSTEP, typename C>
+template <bool INV, int CPG, int STRIDE, int CSTEP, typename C, bool XL = false>
 __device__ __forceinline__ void ring8_pass3(C *cols, int group, int ncol, const Bases8 &bs, const C (&w3)[7],
                                             C (&v)[CPG][8], bool store) {
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
         const int c = group + CSTEP * u;
         if (c < ncol) {
+            constexpr int kRun = XL ? 72 : 68;  // slots per run of 64 positions
             C *col = cols + c * STRIDE + bs.bj;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
+            for (int r = 0; r < 8; ++r) v[u][r] = col[kRun * r];
 #pragma unroll
             for (int r = 1; r < 8; ++r) v[u][r] = c_mul(v[u][r], w3[r - 1]);
             dft8<INV>(v[u]);
             if (store) {
 #pragma unroll
-                for (int r = 0; r < 8; ++r) col[68 * r] = v[u][r];
+                for (int r = 0; r < 8; ++r) col[kRun * r] = v[u][r];
             }
         }
     }
@@ -475,8 +487,8 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
             }
         }
         group_sync(group);
-        ring8_pass2<false, CPG, kColR, 8>(cols, group, NC, bs, w2, v);
-        ring8_pass3<false, CPG, kColR, 8>(cols, group, NC, bs, w3, v, true);
+        ring8_pass2<false, CPG, kColR, 8, C, true>(cols, group, NC, bs, w2, v);
+        ring8_pass3<false, CPG, kColR, 8, C, true>(cols, group, NC, bs, w3, v, true);
     }
     __syncthreads();
 
@@ -497,7 +509,7 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
         const int p = tid;
         const int q = p <= kN8 / 2 ? p : kN8 - p;
         const bool mir = p > kN8 / 2;
-        C *mp = cols + pad16(p);
+        C *mp = cols + padx16(p);
         if (mir) {
 #pragma unroll
             for (int l = 0; l < L; ++l) {
@@ -573,7 +585,7 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
         if (c < NC) {
             const C *col = cols + c * kColR + bs.bj;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) v[u][r] = col[68 * r];
+            for (int r = 0; r < 8; ++r) v[u][r] = col[72 * r];  // exchange layout
         }
     }
     group_sync(group);
@@ -588,8 +600,8 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
         }
     }
     group_sync(group);
-    ring8_pass2<true, CPG, kColR, 8>(cols, group, NC, bs, w2, v);
-    ring8_pass3<true, CPG, kColR, 8>(cols, group, NC, bs, w3, v, false);
+    ring8_pass2<true, CPG, kColR, 8, C, true>(cols, group, NC, bs, w2, v);
+    ring8_pass3<true, CPG, kColR, 8, C, true>(cols, group, NC, bs, w3, v, false);
 #pragma unroll
     for (int u = 0; u < CPG; ++u) {
         const int c = group + 8 * u;
@@ -606,12 +618,13 @@ __global__ void __launch_bounds__(544, 1) k_columns_ring8(float2 *__restrict__ s
 // ---------------------------------------------------------------------------
 // Row transforms for Px = 512: 16 rows of one plane per 256-thread block, the
 // rows taken in pairs as one complex transform (z = row_a + i row_b), two
-// pairs per 64-thread group.  Same shared-memory layout as the column kernel
-// (one pad slot per 16); the column stride is 4 mod 16 words so that the
-// untangling step, where a warp reads 8 columns at 4 frequencies, spreads over
-// all banks.  Rows a and b of a pair are adjacent in the spectrum ([kx][y]), so
-// both are moved with one 16-byte access (ny even).
-constexpr int kColRow = kN8 + kN8 / 16 + 4;
+// pairs per 64-thread group.  The data enter pass 1 and leave pass 2 in the
+// exchange layout (padx16; pass-1 outputs in pad16); the column stride of 574
+// slots (padx16(511) = 570) makes the untangling step, where a warp reads 8
+// columns at 4 frequencies, take at most 3 wavefronts per access.  Rows a and
+// b of a pair are adjacent in the spectrum ([kx][y]), so both are moved with
+// one 16-byte access (ny even).
+constexpr int kColRow = 574;
 
 // Two consecutive complex values as one 16-byte access (16-byte aligned).
 __device__ __forceinline__ void store_pair(float2 *o, float2 a, float2 b) {
@@ -676,8 +689,8 @@ __global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
         for (int r = 0; r < 8; ++r) col[r] = v[h][r];
     }
     group_sync(group);
-    ring8_pass2<false, 2, kColRow, 4>(buf, group, 8, bs, w2, v);
-    ring8_pass3<false, 2, kColRow, 4>(buf, group, 8, bs, w3, v, true);
+    ring8_pass2<false, 2, kColRow, 4, C, true>(buf, group, 8, bs, w2, v);
+    ring8_pass3<false, 2, kColRow, 4, C, true>(buf, group, 8, bs, w3, v, true);
     __syncthreads();
     // A[k] = (Z[k] + conj Z[-k]) / 2,  B[k] = (Z[k] - conj Z[-k]) / (2i): one
     // item per (kx, pair), rows a and b written together
@@ -688,7 +701,7 @@ __global__ void __launch_bounds__(256) k_rows_forward8(const T *__restrict__ m,
         const int ya = y0 + 2 * q;
         if (ya >= ny) continue;
         const C *zb = buf + q * kColRow;
-        const C z1 = zb[pad16(kx)], z2 = zb[pad16((kN8 - kx) & (kN8 - 1))];
+        const C z1 = zb[padx16(kx)], z2 = zb[padx16((kN8 - kx) & (kN8 - 1))];
         const C a = C{(T)0.5 * (z1.x + z2.x), (T)0.5 * (z1.y - z2.y)};
         const C b = C{(T)0.5 * (z1.y + z2.y), (T)0.5 * (z2.x - z1.x)};
         C *o = sp + (size_t)kx * ny + ya;
@@ -745,10 +758,10 @@ __global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>:
         if (kx == 0) {
             A.y = 0;
             B.y = 0;
-            zb[pad16(0)] = C{A.x, B.x};
+            zb[padx16(0)] = C{A.x, B.x};
         } else {
-            zb[pad16(kx)] = C{A.x - B.y, A.y + B.x};
-            zb[pad16(kN8 - kx)] = C{A.x + B.y, B.x - A.y};
+            zb[padx16(kx)] = C{A.x - B.y, A.y + B.x};
+            zb[padx16(kN8 - kx)] = C{A.x + B.y, B.x - A.y};
         }
     }
     if (threadIdx.x < 8) {
@@ -756,7 +769,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>:
         C A = C{0, 0}, B = C{0, 0};
         if (ya < ny) A = p[0];
         if (ya + 1 < ny) B = p[1];
-        zb[pad16(half)] = C{A.x, B.x};  // A, B real at Nyquist
+        zb[padx16(half)] = C{A.x, B.x};  // A, B real at Nyquist
     }
     __syncthreads();
     // inverse transforms: pass 1 in shared memory, pass 3 straight to global
@@ -768,7 +781,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>:
     for (int h = 0; h < 2; ++h) {
         const C *col = buf + (group + 4 * h) * kColRow + bs.bj;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[h][q] = col[68 * q];
+        for (int q = 0; q < 8; ++q) v[h][q] = col[72 * q];  // exchange layout
     }
     group_sync(group);
 #pragma unroll
@@ -779,8 +792,8 @@ __global__ void __launch_bounds__(256) k_rows_inverse8(const typename cpx_of<T>:
         for (int q = 0; q < 8; ++q) col[q] = v[h][q];
     }
     group_sync(group);
-    ring8_pass2<true, 2, kColRow, 4>(buf, group, 8, bs, w2, v);
-    ring8_pass3<true, 2, kColRow, 4>(buf, group, 8, bs, w3, v, false);
+    ring8_pass2<true, 2, kColRow, 4, C, true>(buf, group, 8, bs, w2, v);
+    ring8_pass3<true, 2, kColRow, 4, C, true>(buf, group, 8, bs, w3, v, false);
     T *hp = H + (size_t)plane * ny * nx;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {

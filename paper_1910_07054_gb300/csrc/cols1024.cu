@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_inverse1024(const fl
     const int group = threadIdx.x >> 6, j = threadIdx.x & 63;
     const int g = g0 + group;
     const int ng = min(kF10Planes, planes - g0);
-    f10_load_table(tws, tw, sh);
+    f10_load_table<true>(tws, tw, sh);  // W_64 slots permuted (fft1024.cuh)
     // Y[ky] from row p = bitrev(ky): even frequencies to column a, odd to b
     // (8 loads in flight per thread before their stores)
     const float2 *in = spec2 + (size_t)kx * 1024 * planes + g0;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_columns_inverse1024(const fl
         v[1][r] = b[bs.bx(r)];
     }
     f10_sync(group);  // pass 1 stores over positions other threads read
-    f10_transform<true>(v, a, b, bs, j, group, tws);
+    f10_transform<true, true>(v, a, b, bs, j, group, tws);
     // y[n] = a[n] + W_1024^-n b[n], n = j + 64 r < ny
     if (g < planes) {
         float2 *dst = spec + ((size_t)g * Kx + kx) * ny;

@@ -40,6 +40,13 @@ constexpr size_t kF10Smem = (size_t)kF10Planes * kF10Plane * sizeof(float2) + kF
 
 __device__ __forceinline__ int f10_pad(int p) { return p + (p >> 4) + 4 * (p >> 6); }
 __device__ __forceinline__ int f10_padA(int p) { return p + (p >> 4); }
+// Slot of W_64^m in its table when it is permuted (PERM): m with its low three
+// bits flipped when bits 4 and 5 of m differ (an involution), so that the
+// pass-2 lookups W_64^{r k mod 64}, k = j mod 8, of every r = 1..7 fall in
+// distinct banks (in plain order r = 4 is 2-way).  The permutation costs a few
+// integer instructions per lookup, which only the inverse column transform
+// gains back (measured).
+__device__ __forceinline__ int f10_w64_slot(int m) { return m ^ (7 * (((m >> 4) ^ (m >> 5)) & 1)); }
 
 __device__ __forceinline__ void f10_sync(int group) {
     asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(64) : "memory");
@@ -73,7 +80,7 @@ struct F10Bases {
 // Passes 1..3 of both 512-point transforms of a plane; v[0] and v[1] hold the
 // pass-1 inputs (positions j + 64 r) on entry and the outputs (positions
 // j + 64 r) on return.  a, b: the plane's two padded columns.
-template <bool INV>
+template <bool INV, bool PERM = false>
 __device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, float2 *b, const F10Bases &bs, int j,
                                               int group, const float2 *tw) {
     float2 *col[2] = {a, b};
@@ -92,12 +99,11 @@ __device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, floa
         for (int r = 0; r < 8; ++r) v[t][r] = col[t][bs.bj + 68 * r];
     f10_sync(group);
     {
-        // W_64^{rk} from the 64-entry table: for the 8 values of k in a warp the
-        // indices r k mod 64 fall in distinct banks (2-way at r = 4)
+        // W_64^{rk} from the 64-entry table
         const int k = j & 7;
 #pragma unroll
         for (int r = 1; r < 8; ++r) {
-            float2 w = tw[512 + ((r * k) & 63)];
+            float2 w = tw[512 + (PERM ? f10_w64_slot((r * k) & 63) : ((r * k) & 63))];
             if (INV) w.y = -w.y;
             v[0][r] = c_mul(v[0][r], w);
             v[1][r] = c_mul(v[1][r], w);
@@ -139,9 +145,11 @@ __device__ __forceinline__ void f10_transform(float2 (&v)[2][8], float2 *a, floa
 
 // The three tables from the plan's table tw of W_{2^(10 + sh)}^k, k below half
 // its period (W_1024^(m + 512) = -W_1024^m).
+template <bool PERM = false>
 __device__ __forceinline__ void f10_load_table(float2 *tws, const float2 *__restrict__ tw, int sh) {
     for (int k = threadIdx.x; k < kF10Tw; k += blockDim.x) {
-        const int m = k < 512 ? k : (k < 576 ? 16 * (k - 512) : 2 * (k - 576));  // exponent of W_1024, < 1024
+        // exponent of W_1024 (< 1024) held by slot k
+        const int m = k < 512 ? k : (k < 576 ? 16 * (PERM ? f10_w64_slot(k - 512) : k - 512) : 2 * (k - 576));
         float2 w = tw[(m & 511) << sh];
         if (m & 512) {
             w.x = -w.x;
