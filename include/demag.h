@@ -361,6 +361,33 @@ demag_status demag_apply_timed(demag_plan_t plan, const void *m, double Ms, void
 demag_status demag_plan_info(demag_plan_t plan, long long *out);
 
 /*
+ * demag_plan_compress - drop the negligible layer blocks of a split-precision
+ * plan's tensor (the compressed tensor of the survey's next steps).
+ *
+ * Sec. 3.2: the hybrid's cost grows with the layer pairs, whose tensor the
+ * contraction streams once per apply.  In the in-plane Fourier domain the
+ * coupling of two layers decays like exp(-|k| Z) with their distance Z, so
+ * at high frequencies the 8 x 8 blocks of distant layers hold values far
+ * below float resolution.  This call keeps, entry by entry, only the blocks
+ * with a value of at least tol times the largest value of its component in
+ * the whole tensor, and stores them contiguously with a 64-bit block mask and
+ * an offset per entry; the contraction then neither reads nor multiplies the
+ * dropped blocks' values (they count as zero).
+ *
+ *   plan          a DEMAG_PREC_SPLIT_TF32 or DEMAG_PREC_SPLIT_BF16 plan on
+ *                 path 6 or 7 (even L <= 64, max_batch <= 16)
+ *   tol           0 <= tol < 1; 0 keeps every block that holds a nonzero
+ *   stored_bytes  out (may be NULL): bytes of the compressed tensor
+ *
+ * The call synchronises the device and replaces the plan's tensor.  After it
+ * the plan runs paths 6 and 7 only, and demag_plan_tensor refuses.  Errors:
+ * DEMAG_EINVAL (NULL plan, tol outside [0, 1)), DEMAG_EUNSUPPORTED (another
+ * precision or path, or already compressed), DEMAG_ENOMEM / DEMAG_ECUDA
+ * (the plan keeps its uncompressed tensor).
+ */
+demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_bytes);
+
+/*
  * demag_plan_tensor - copy of the stored Fourier-space tensor.
  *
  * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,

@@ -77,6 +77,8 @@ def lib():
     L.demag_plan_info.restype = i
     L.demag_plan_tensor.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.demag_plan_tensor.restype = i
+    L.demag_plan_compress.argtypes = [vp, d, ctypes.POINTER(ctypes.c_size_t)]
+    L.demag_plan_compress.restype = i
     L.demag_tensor_points.argtypes = [i, vp, vp, vp]
     L.demag_tensor_points.restype = i
     L.demag_plan_set_path.argtypes = [vp, i]
@@ -307,6 +309,14 @@ def demag_plan_tensor(plan, out, stream=None):
     return out
 
 
+def demag_plan_compress(plan, tol):
+    """Drop the tensor blocks below tol of their component's maximum
+    (demag_plan_compress in demag.h); returns the compressed tensor's bytes."""
+    n = ctypes.c_size_t(0)
+    _check(lib().demag_plan_compress(ctypes.c_void_p(plan), float(tol), ctypes.byref(n)), "demag_plan_compress")
+    return int(n.value)
+
+
 def demag_tensor_points(geom, out, stream=None):
     """geom: CUDA float64 [n, 9]; out: CUDA float64 [n, 6]."""
     import torch
@@ -452,6 +462,13 @@ class Plan:
         self.handle = demag_plan_create_equidistant(nx, ny, nz, dx, dy, dz, precision, max_batch, stream)
         self.info = demag_plan_info(self.handle)
         return self
+
+    def compress(self, tol):
+        """Block-compress the plan's tensor (split-precision plans on path 6
+        or 7); returns the stored bytes."""
+        n = demag_plan_compress(self.handle, tol)
+        self.info = demag_plan_info(self.handle)
+        return n
 
     def close(self):
         if self.handle:

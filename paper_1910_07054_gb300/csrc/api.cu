@@ -65,6 +65,8 @@ static void free_plan(demag_plan *p) {
     cudaFree(p->d_dH);
     cudaFree(p->d_dot);
     cudaFree(p->d_twz);
+    cudaFree(p->d_bmask);
+    cudaFree(p->d_bfirst);
     if (p->h_timeouts) cudaFreeHost(p->h_timeouts);
     for (auto &set : p->pipe_ev)
         for (cudaEvent_t ev : set)
@@ -565,6 +567,8 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.split = plan->split;
     a.contract_mode = plan->contract_mode;
     a.natural = plan->natural;
+    a.bmask = plan->d_bmask;
+    a.bfirst = plan->d_bfirst;
     a.twz = plan->d_twz;
     a.log2Pz = plan->log2Pz;
     a.Ms = Ms;
@@ -758,6 +762,8 @@ demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     if (plan->umajor) {
         const bool tc5 = tc5_supported(plan->L, plan->max_batch, plan->npairs);
         if (path == 0) path = !tc5 ? 4 : (plan->precision == DEMAG_PREC_SPLIT_BF16 ? 7 : 6);
+        if (plan->d_bmask && path != 6 && path != 7)
+            return fail(DEMAG_EUNSUPPORTED, "a compressed tensor is read by paths 6 and 7 only");
         if (path != 3 && path != 4 && path != 6 && path != 7)
             return fail(DEMAG_EUNSUPPORTED, "split-precision plans run path 3, 4, 6 or 7");
         if ((path == 6 || path == 7) && !tc5)
@@ -856,6 +862,30 @@ demag_status demag_tensor_points_dt(int n, const double *geom, double *out, doub
     return DEMAG_OK;
 }
 
+demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_bytes) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    if (!(tol >= 0.0) || !(tol < 1.0)) return fail(DEMAG_EINVAL, "tol must be in [0, 1)");
+    if (!plan->umajor || plan->method != 0 || (plan->contract_mode != 3 && plan->contract_mode != 4))
+        return fail(DEMAG_EUNSUPPORTED, "compression needs a split-precision plan on path 6 or 7");
+    if (plan->d_bmask) return fail(DEMAG_EUNSUPPORTED, "the plan's tensor is already compressed");
+    DEMAG_CUDA(cudaDeviceSynchronize());  // no apply may be reading the tensor
+    float *out = nullptr;
+    size_t bytes = 0;
+    unsigned long long *mask = nullptr;
+    unsigned *first = nullptr;
+    const size_t nent = (size_t)plan->Kx * plan->Qy;
+    cudaError_t e = compress_tensor((const float *)plan->d_tensor, nent, plan->L, tol, &out, &bytes, &mask, &first, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor compression");
+    cudaFree(plan->d_tensor);
+    plan->d_tensor = out;
+    plan->tensor_bytes = bytes;
+    plan->d_bmask = mask;
+    plan->d_bfirst = first;
+    plan->compress_tol = tol;
+    if (stored_bytes) *stored_bytes = bytes;
+    return DEMAG_OK;
+}
+
 demag_status demag_plan_info(demag_plan_t plan, long long *out) {
     if (!plan || !out) return fail(DEMAG_EINVAL, "plan or out is NULL");
     out[0] = plan->nx;
@@ -876,6 +906,7 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out) {
 
 demag_status demag_plan_tensor(demag_plan_t plan, void *out, size_t bytes, void *stream) {
     if (!plan || !out) return fail(DEMAG_EINVAL, "plan or out is NULL");
+    if (plan->d_bmask) return fail(DEMAG_EUNSUPPORTED, "the plan's tensor is compressed (demag_plan_compress)");
     if (bytes != plan->tensor_bytes)
         return fail(DEMAG_EINVAL, "out must hold exactly " + std::to_string(plan->tensor_bytes) + " bytes");
     DEMAG_CUDA(cudaMemcpyAsync(out, plan->d_tensor, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));

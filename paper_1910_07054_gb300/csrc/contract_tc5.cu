@@ -94,7 +94,7 @@ __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs, int kc = 1
     // a state's 3L complex values, padded so that consecutive states start 16
     // bytes apart modulo 128 (the 8 states a warp reads at once hit 8 bank groups)
     s.seg = 3 * L + ((2 - (3 * L) % 16) + 16) % 16;
-    s.raw_bytes = round128((size_t)s.NB * 4);
+    s.raw_bytes = round128((size_t)s.NB * 4 + 256);  // + a zero block for dropped blocks of compressed tensors
     s.rows_bytes = round128((size_t)2 * B * s.seg * 8);
     s.in_bytes = s.raw_bytes + s.rows_bytes;  // one input buffer (two of them)
     s.s_bytes = (size_t)kTcN * 64;  // N rows x 64 bytes of K
@@ -182,16 +182,22 @@ __device__ __forceinline__ void tc_mma_chunk(unsigned dt, unsigned at, uint64_t 
 
 }  // namespace
 
-template <bool BF>
+// CMP: the plan's tensor is block-compressed (compress.cu): entry e holds its
+// kept blocks only, bmask[e] tells which, bfirst[e] where they start.
+template <bool BF, bool CMP>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restrict__ spec2,
                                                                const float *__restrict__ tensor_um,
                                                                const float *__restrict__ ratio, int L, int B,
-                                                               int log2Px, int log2Py, int npairs) {
+                                                               int log2Px, int log2Py, int npairs,
+                                                               const unsigned long long *__restrict__ bmask,
+                                                               const unsigned *__restrict__ bfirst) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t st_full[kTcStages], st_empty[kTcStages], d_full[2], d_empty[2];
     __shared__ __align__(8) uint64_t in_full[2], in_empty[2];  // the entry's tensor and state rows
     __shared__ unsigned tmem_slot;
     __shared__ __align__(16) float s_itau[64];
+    __shared__ int s_bkept[2];       // compressed tensor: kept blocks of the entry in each input buffer
+    __shared__ int s_boff[2][64];    // and the byte offset in a component row of block (I, J), -1 if dropped
     __shared__ int s_abort;
     constexpr int KC = TcKC<BF>::value;  // K columns per chunk
     constexpr int PW = Split<BF>::kPerWord;
@@ -218,6 +224,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         s_abort = 0;
     }
     if (tid < 64) s_itau[tid] = tid < L ? ratio[tid * L] : 0.f;  // t_0 / t_l
+    if (CMP && tid < 128)  // the zero block at the end of each input buffer's tensor part
+        reinterpret_cast<float *>(smem + (tid >> 6) * sh.in_bytes + sh.raw_bytes - 256)[tid & 63] = 0.f;
     if (warp == kTcMma) tc_alloc(&tmem_slot, kTcCols);
     tc_fence_before();
     __syncthreads();
@@ -251,8 +259,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
             int kx, u, p1, p2, npos;
             bool mir0;
             entry(lf, kx, u, p1, p2, npos, mir0);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tensor_um + ((size_t)kx * Qy + u) * sh.NB),
-                         "r"((unsigned)sh.NB * 4) : "memory");
+            if (CMP) {
+                const size_t ent = (size_t)kx * Qy + u;
+                const unsigned tb = 6u * 256u * (unsigned)__popcll(bmask[ent]);
+                if (tb)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tensor_um + (size_t)bfirst[ent] * 64),
+                                 "r"(tb) : "memory");
+            } else {
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tensor_um + ((size_t)kx * Qy + u) * sh.NB),
+                             "r"((unsigned)sh.NB * 4) : "memory");
+            }
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(spec2 + ((size_t)kx * Py + p1) * planes),
                          "r"((unsigned)planes * 8) : "memory");
             if (npos == 2)
@@ -274,9 +290,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
             bool mir0;
             entry(lf, kx, u, p1, p2, npos, mir0);
             unsigned char *in = smem + (size_t)buf * sh.in_bytes;
+            unsigned tb = (unsigned)sh.NB * 4;
+            const float *tsrc = tensor_um + ((size_t)kx * Qy + u) * sh.NB;
+            if (CMP) {
+                // the header (kept count, block offsets) is written by all lanes
+                // before the arrival that publishes it
+                const size_t ent = (size_t)kx * Qy + u;
+                unsigned long long m = 0;
+                unsigned f = 0;
+                if (lane == 0) {
+                    m = bmask[ent];
+                    f = bfirst[ent];
+                }
+                m = __shfl_sync(0xffffffffu, m, 0);
+                f = __shfl_sync(0xffffffffu, f, 0);
+                const int nbk = ub_nb(L);
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int idx = lane + 32 * h2, I = idx >> 3, J = idx & 7;
+                    int bo = -1;
+                    if (I < nbk && J < nbk) {
+                        const int b = (I <= J ? ub_blk(I, J, nbk) : ub_blk(J, I, nbk)) >> 6;
+                        if ((m >> b) & 1ull) bo = 256 * __popcll(m & ((1ull << b) - 1ull));
+                    }
+                    s_boff[buf][idx] = bo;
+                }
+                if (lane == 0) s_bkept[buf] = __popcll(m);
+                tb = 6u * 256u * (unsigned)__popcll(m);
+                tsrc = tensor_um + (size_t)f * 64;
+                __syncwarp();
+            }
             if (lane == 0) {
-                mbar_arrive_expect_tx(&in_full[buf], (unsigned)sh.NB * 4 + (unsigned)(npos * B) * segb);
-                bulk_copy_g2s(in, tensor_um + ((size_t)kx * Qy + u) * sh.NB, (unsigned)sh.NB * 4, &in_full[buf]);
+                mbar_arrive_expect_tx(&in_full[buf], tb + (unsigned)(npos * B) * segb);
+                if (tb) bulk_copy_g2s(in, tsrc, tb, &in_full[buf]);
             }
             __syncwarp();
             for (int c = lane; c < npos * B; c += 32) {
@@ -322,12 +368,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         // per source component ci: byte offset of the stored component row, and
         // the sign of blocks on or above the diagonal (-1 for the -K_zz block of
         // A) and below it (there xz and yz also change sign: reciprocity)
-        int offc[3];
+        int offc[3], compc[3];
         float sup[3], slo[3];
 #pragma unroll
         for (int ci = 0; ci < 3; ++ci) {
             const int comp = tc_comp(co, ci);
             const float zs = (co == 2 && ci == 2) ? -1.f : 1.f;
+            compc[ci] = comp;
             offc[ci] = comp * NR * 4;
             sup[ci] = zs;
             slo[ci] = comp >= 4 ? -zs : zs;
@@ -349,6 +396,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
             const int buf = lf & 1;
             if (!mbar_wait(&in_full[buf], (lf >> 1) & 1, &g_tc_timeouts)) ok = false;
             const int inb = buf * (int)sh.in_bytes;  // this entry's input buffer
+            if (CMP) {
+                const int nk = s_bkept[buf];
+#pragma unroll
+                for (int ci = 0; ci < 3; ++ci) offc[ci] = compc[ci] * nk * 256;  // component rows of nk blocks
+            }
             const bool slive = sact && spq < npos && sb < B;
             const float sy0 = ((spq == 0) == mir0) ? -1.f : 1.f;  // m_y negated at the mirrored position
             for (int ch = 0; ch < sh.nch && ok; ++ch) {
@@ -367,20 +419,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                         if (kc0 < R) {
                             // the sub-block is layer block J of source component ci
                             const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), J = (kc0 - ci * Lp) >> 3;
-                            const int off = inb + (ci == 0 ? offc[0] : (ci == 1 ? offc[1] : offc[2]));
+                            int off = inb + (ci == 0 ? offc[0] : (ci == 1 ? offc[1] : offc[2]));
                             float sg;
+                            if (CMP) {
+                                // the kept block's place, or the zero block that follows
+                                // the raw buffer (a dropped block reads as zeros, without
+                                // a branch of its own)
+                                const int bo = s_boff[buf][8 * I + J];
+                                off = bo >= 0 ? off + bo : inb + (int)sh.raw_bytes - 256;
+                            }
                             if (I <= J) {
                                 // row i8 of block (I, J): 8 consecutive values
-                                const float4 *src =
-                                    reinterpret_cast<const float4 *>(smem + off + 4 * (ub_blk(I, J, nb) + 8 * i8));
+                                const float4 *src = reinterpret_cast<const float4 *>(
+                                    smem + off + (CMP ? 0 : 4 * ub_blk(I, J, nb)) + 32 * i8);
                                 const float4 x0 = src[0], x1 = src[1];
                                 vs8[0] = x0.x, vs8[1] = x0.y, vs8[2] = x0.z, vs8[3] = x0.w;
                                 vs8[4] = x1.x, vs8[5] = x1.y, vs8[6] = x1.z, vs8[7] = x1.w;
                                 sg = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
                             } else {
                                 // column i8 of block (J, I): M(i, 8 J + e) = s_c M(8 J + e, i)
-                                const float *src =
-                                    reinterpret_cast<const float *>(smem + off + 4 * (ub_blk(J, I, nb) + i8));
+                                const float *src = reinterpret_cast<const float *>(
+                                    smem + off + (CMP ? 0 : 4 * ub_blk(J, I, nb)) + 4 * i8);
 #pragma unroll
                                 for (int e = 0; e < 8; ++e) vs8[e] = src[8 * e];
                                 sg = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
@@ -558,7 +617,9 @@ bool tc5_supported(int L, int B, int npairs) {
 
 cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st) {
     const TcShape sh = tc_shape(a.L, a.B, a.npairs, bf16 ? TcKC<true>::value : TcKC<false>::value);
-    auto kernel = bf16 ? k_contract_tc5<true> : k_contract_tc5<false>;
+    const bool cmp = a.bmask != nullptr;
+    auto kernel = bf16 ? (cmp ? k_contract_tc5<true, true> : k_contract_tc5<true, false>)
+                       : (cmp ? k_contract_tc5<false, true> : k_contract_tc5<false, false>);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.total)) != cudaSuccess)
         return e;
@@ -568,7 +629,7 @@ cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st) 
     const int nent = ((1 << a.log2Px) / 2 + 1) * ((1 << a.log2Py) / 2 + 1);
     const int grid = nent < nsm ? nent : nsm;
     kernel<<<grid, kTcThreads, sh.total, st>>>((float2 *)a.spec2, (const float *)a.tensor, (const float *)a.ratio,
-                                               a.L, a.B, a.log2Px, a.log2Py, a.npairs);
+                                               a.L, a.B, a.log2Px, a.log2Py, a.npairs, a.bmask, a.bfirst);
     return cudaGetLastError();
 }
 

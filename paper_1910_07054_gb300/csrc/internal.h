@@ -89,6 +89,8 @@ struct ApplyArgs {
                             // the tcgen05 tensor cores (3xTF32, TMEM accumulators), 4 the same
                             // with 3xBF16, 5 the z-convolution of the equidistant method
     int natural = 0;      // 512-point column kernel, tensor in natural folded-ky order
+    const unsigned long long *bmask = nullptr;  // block-compressed tensor: kept blocks per entry
+    const unsigned *bfirst = nullptr;           // and the entry's first block (units of 64 floats)
     cudaEvent_t *inner_ev = nullptr;  // split path, optional [4]: before and after its 3 kernels
     const void *in_scale = nullptr;   // optional [L]: m of layer l scaled on input
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
@@ -130,6 +132,12 @@ bool tc5_supported(int L, int B, int npairs);
 cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st);
 // The same count for the tcgen05 contraction kernel.
 cudaError_t read_tc_timeouts(unsigned *dst, cudaStream_t st);
+// Block-sparse copy of a dense-product tensor (compress.cu): nent entries of the
+// blocked layout for L layers; blocks whose values are all below tol times their
+// component's maximum are dropped.  On success *out (device, *out_bytes bytes),
+// *mask and *first (device, nent each) are new allocations owned by the caller.
+cudaError_t compress_tensor(const float *tensor, size_t nent, int L, double tol, float **out, size_t *out_bytes,
+                            unsigned long long **mask, unsigned **first, cudaStream_t st);
 
 // Equidistant method of Eq. FFT_3D (fft3d.cu): the z-convolution that
 // replaces the layer contraction (contract_mode 5), and the z-transform of the
@@ -170,7 +178,10 @@ struct demag_plan {
     void *d_spec2 = nullptr;      // split path workspace
     int split = 0;                // 1: split path
     int contract_mode = 0;        // split path contraction (see ApplyArgs)
-    int umajor = 0;               // tensor layout [Kx][Qy][6][npairs padded] (split-TF32 plans)
+    int umajor = 0;               // blocked tensor layout [Kx][Qy][6][blocks] (dense-product plans)
+    unsigned long long *d_bmask = nullptr;  // after demag_plan_compress: kept blocks per entry
+    unsigned *d_bfirst = nullptr;           // and each entry's first block
+    double compress_tol = -1.0;             // < 0: not compressed
     int natural = 0;              // fused 512-point column kernel, natural folded-ky tensor
     int method = 0;               // 0 hybrid (Eq. FFT_v2), 1 equidistant 3D FFT (Eq. FFT_3D)
     int log2Pz = 0;               // equidistant plans: padded z size

@@ -62,6 +62,7 @@ def test_other_entry_points_reject_null_and_bad_sizes():
     assert lib.demag_tensor_points(5, None, None, None) == 1
     assert lib.demag_plan_info(None, None) == 1
     assert lib.demag_plan_tensor(None, None, 0, None) == 1
+    assert lib.demag_plan_compress(None, 1e-8, None) == 1
     assert lib.demag_destroy(None) == 0
 
 

@@ -135,3 +135,68 @@ def test_split_bf16_plan_defaults_to_the_bf16_tcgen05_path():
         plan.close()
         ref = odm.hybrid(reading_kernels(nx, ny, 2.0, 2.0, th), m, 8e5)
         assert rel_l2(H.double().cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("prec,nx,ny,th,shrinks", [
+    (dm.PREC_SPLIT_BF16, 64, 48, tuple(np.round(np.linspace(0.6, 2.4, 20), 3)), False),
+    (dm.PREC_SPLIT_TF32, 40, 36, tuple(np.round(np.linspace(0.5, 3.0, 24), 3)), False),
+    (dm.PREC_SPLIT_BF16, 32, 24, (1.0,) * 8 + (100.0, 100.0) + (1.0,) * 8, True),
+    (dm.PREC_SPLIT_BF16, 13, 9, (1.0, 0.5, 2.0, 0.8), False),
+])
+def test_compressed_tensor_field_and_adjoint_match_oracle(prec, nx, ny, th, shrinks):
+    """demag_plan_compress drops the 8 x 8 layer blocks below 1e-8 of their
+    component's maximum; the field and the adjoint of the compressed plan stay
+    within the float bound of the oracle.  The stack with two 100 nm spacer
+    layers puts its last block 200 nm above the first, so that block pair
+    drops at all but the lowest in-plane frequencies."""
+    B = 3
+    m = inputs.random_unit_vectors((B, len(th), ny, nx), seed=17)
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=prec, max_batch=B)
+    full = plan.info
+    nb = (len(th) + 7) // 8
+    full_bytes = (full["Px"] // 2 + 1) * (full["Py"] // 2 + 1) * 6 * 64 * nb * (nb + 1) // 2 * 4
+    stored = plan.compress(1e-8)
+    assert 0 < stored <= full_bytes
+    if shrinks:
+        assert stored < 0.95 * full_bytes, (stored, full_bytes)
+    mt = torch.tensor(m, dtype=torch.float32, device="cuda")
+    H = plan.apply(mt, 8e5)
+    out = torch.empty_like(mt)
+    dm.demag_apply_adjoint(plan.handle, mt, 3.0, out, info=plan.info)
+    torch.cuda.synchronize()
+    plan.close()
+    assert dm.demag_wait_timeouts() == 0
+    K = reading_kernels(nx, ny, 2.0, 2.0, th)
+    assert rel_l2(H.double().cpu().numpy(), odm.hybrid(K, m, 8e5)) < 1e-5
+    KT = np.transpose(K[:, :, :, ::-1, ::-1], (1, 0, 2, 3, 4))
+    assert rel_l2(out.double().cpu().numpy(), odm.hybrid(KT, m, 3.0)) < 1e-5
+
+
+def test_compressed_plan_restrictions():
+    """After compression only paths 6 and 7 run and the tensor is not exported;
+    a second compression, other precisions and a bad tolerance are refused."""
+    th = (1.0, 0.5, 2.0, 0.8)
+    plan = dm.Plan(12, 10, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=2)
+    try:
+        with pytest.raises(dm.DemagError):
+            plan.compress(-1.0)
+        with pytest.raises(dm.DemagError):
+            plan.compress(1.0)
+        plan.compress(0.0)
+        with pytest.raises(dm.DemagError):
+            plan.compress(1e-8)
+        for path in (3, 4):
+            with pytest.raises(dm.DemagError):
+                dm.demag_plan_set_path(plan.handle, path)
+        for path in (6, 7, 0):
+            dm.demag_plan_set_path(plan.handle, path)
+        with pytest.raises(dm.DemagError):
+            dm.demag_plan_tensor(plan.handle, torch.empty(16, dtype=torch.float32, device="cuda"))
+    finally:
+        plan.close()
+    p32 = dm.Plan(12, 10, 2.0, 2.0, th, precision=dm.PREC_FP32)
+    try:
+        with pytest.raises(dm.DemagError):
+            p32.compress(1e-8)
+    finally:
+        p32.close()
