@@ -362,7 +362,7 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
 
 /*
  * demag_plan_compress - drop the negligible layer blocks of a split-precision
- * plan's tensor (the compressed tensor of the survey's next steps).
+ * plan's tensor (a block-sparse compressed tensor).
  *
  * Sec. 3.2: the hybrid's cost grows with the layer pairs, whose tensor the
  * contraction streams once per apply.  In the in-plane Fourier domain the
