@@ -105,3 +105,32 @@ def test_surrogate_newton_needs_fewer_exact_solves():
     n_sur = next(s for (t, hz, s, kind) in sur if abs(t - t_star) < 1e-3)
     assert abs(sur[-1][0] - t_star) < 1e-3
     assert n_sur < n_exact, (n_sur, n_exact, exact, sur)
+
+
+@pytest.fixture(scope="module")
+def _samples_256():
+    solver = sg.ExactSolver(256, 2.0)
+    T, Y = sg.generate_samples(solver, inputs.opt_samples(2000, seed=0))
+    return solver, T, Y
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_surrogate_newton_needs_fewer_exact_solves_at_256(_samples_256, seed):
+    """The same optimisation on the 256 x 256 x 8 stack of the optimisation
+    workload (2000 solver samples, layer 5 in [0.5, 5] nm, the others +-10 %):
+    for each of three trainings the surrogate-proposed Newton steps reach the
+    optimum within 1e-3 nm in fewer exact solves than exact Newton."""
+    solver, T, Y = _samples_256
+    net = sg.Surrogate(seed=seed)
+    hist = net.fit(T[:1800], Y[:1800], steps=4000, lr=3e-3)
+    assert hist[-1][1] < 1e-2
+    t0 = inputs.OPT_BASE.copy()
+    solver.solves = 0
+    exact = sg.newton_exact(solver, t0, tol=1e-6)
+    t_star = exact[-1][0]
+    n_exact = next(s for (t, hz, s) in exact if abs(t - t_star) < 1e-3)
+    solver.solves = 0
+    sur = sg.newton_surrogate(solver, net, t0, tol=1e-6)
+    n_sur = next(s for (t, hz, s, kind) in sur if abs(t - t_star) < 1e-3)
+    assert abs(sur[-1][0] - t_star) < 1e-3
+    assert n_sur < n_exact, (n_sur, n_exact)
