@@ -388,6 +388,89 @@ demag_status demag_plan_info(demag_plan_t plan, long long *out);
 demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_bytes);
 
 /*
+ * Frequency-sharded apply: the three steps of Eq. FFT_v2 as separate calls, so
+ * that several processes (one GPU each) can share one apply.  The row
+ * transforms (x) work plane by plane, a plane being one (state, layer,
+ * component) of m, plane index p = (b * L + l) * 3 + c; the column transforms
+ * (y), the sum over source layers and the inverse column transforms work kx
+ * by kx over every plane.  A rank transforms the rows of its planes, an
+ * all-to-all (the caller's: NCCL, gloo, copies) gives each rank every plane
+ * at its own x-frequencies, each rank runs its slab with only that slab of the
+ * tensor, a second all-to-all returns the slabs, and each rank runs the
+ * inverse row transforms of its planes.  The result is that of demag_apply,
+ * bit for bit: every column, entry and row is computed by the same kernels.
+ * Sec. 3.1 defines the steps; the split among ranks is this library's.
+ *
+ * The row spectrum of a plane is Kx = Px / 2 + 1 x-frequencies of ny complex
+ * values each (frequency-major: [kx][y]); complex values are two reals of the
+ * plan's type (float, or double for DEMAG_PREC_FP64), interleaved.  Every
+ * pointer is DEVICE memory on the plan's device, owned by the caller; the calls
+ * are asynchronous on `stream` (NULL: the legacy default stream) and report
+ * bounded-wait timeouts like demag_apply.
+ */
+
+/*
+ * demag_plan_keep_slab - keep only the x-frequencies k0 <= kx < k1 of the
+ * plan's tensor (and shrink its column workspace to them), freeing the rest.
+ *
+ *   plan     a hybrid plan on the split path (DEMAG_PREC_SPLIT_TF32 or
+ *            DEMAG_PREC_SPLIT_BF16 plans, or another plan after
+ *            demag_plan_set_path(plan, 2)); not compressed
+ *   k0, k1   0 <= k0 < k1 <= Px / 2 + 1
+ *
+ * Synchronises the device.  Afterwards the plan runs demag_columns_slab on
+ * sub-ranges of [k0, k1) and the row calls below; demag_apply and every call
+ * built on it return DEMAG_EUNSUPPORTED, and demag_plan_tensor copies out the
+ * slab.  Errors: DEMAG_EINVAL (NULL plan, range), DEMAG_EUNSUPPORTED (another
+ * path or method, a compressed tensor, already a slab), DEMAG_ENOMEM /
+ * DEMAG_ECUDA.
+ */
+demag_status demag_plan_keep_slab(demag_plan_t plan, int k0, int k1);
+
+/*
+ * demag_rows_forward - forward row transforms (x) of planes p0 <= p < p1.
+ *
+ *   m     the batch's magnetisation [B][L][3][ny][nx] (the layout of
+ *         demag_apply); planes p0 .. p1 - 1 are read
+ *   spec  out: [p1 - p0][Kx][ny] complex, the planes' row spectra
+ *   0 <= p0 < p1 <= max_batch * L * 3
+ *
+ * Errors: DEMAG_EINVAL (NULL pointer, plane range), DEMAG_ECUDA.
+ */
+demag_status demag_rows_forward(demag_plan_t plan, const void *m, int p0, int p1, void *spec, void *stream);
+
+/*
+ * demag_columns_slab - column transforms, layer sum (Eq. FFT_v2) and inverse
+ * column transforms of every plane at the x-frequencies k0 <= kx < k1, in place.
+ *
+ *   spec  in/out: [B * L * 3][k1 - k0][ny] complex, the row spectra of all
+ *         planes of a batch of B states at those x-frequencies
+ *   k0, k1  within the plan's tensor (all of [0, Px / 2 + 1), or the range
+ *           kept by demag_plan_keep_slab)
+ *   B     states, 1 <= B <= max_batch
+ *
+ * Uses the plan's column workspace: calls on one plan must not overlap on the
+ * GPU.  Errors: DEMAG_EINVAL (NULL pointer, range, B), DEMAG_EUNSUPPORTED (a
+ * plan off the split path, equidistant or compressed), DEMAG_ECUDA.
+ */
+demag_status demag_columns_slab(demag_plan_t plan, void *spec, int k0, int k1, int B, void *stream);
+
+/*
+ * demag_rows_inverse - inverse row transforms of planes p0 <= p < p1, cropped
+ * to nx and scaled by -Ms (the stored tensor carries the 1 / (Px Py) of the
+ * inverse transforms): the field H = -Ms N * m of Eq. FFT_v2.
+ *
+ *   spec  [p1 - p0][Kx][ny] complex, the planes' row spectra after the column
+ *         steps (read only)
+ *   H     out: the batch's field [B][L][3][ny][nx]; planes p0 .. p1 - 1 are
+ *         written
+ *
+ * Errors: DEMAG_EINVAL (NULL pointer, plane range, Ms not finite), DEMAG_ECUDA.
+ */
+demag_status demag_rows_inverse(demag_plan_t plan, const void *spec, int p0, int p1, double Ms, void *H,
+                                void *stream);
+
+/*
  * demag_plan_tensor - copy of the stored Fourier-space tensor.
  *
  * out DEVICE, (Px/2+1) * npairs * 6 * QyS values of the plan's real type,

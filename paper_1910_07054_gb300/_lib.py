@@ -79,6 +79,14 @@ def lib():
     L.demag_plan_tensor.restype = i
     L.demag_plan_compress.argtypes = [vp, d, ctypes.POINTER(ctypes.c_size_t)]
     L.demag_plan_compress.restype = i
+    L.demag_plan_keep_slab.argtypes = [vp, i, i]
+    L.demag_plan_keep_slab.restype = i
+    L.demag_rows_forward.argtypes = [vp, vp, i, i, vp, vp]
+    L.demag_rows_forward.restype = i
+    L.demag_columns_slab.argtypes = [vp, vp, i, i, i, vp]
+    L.demag_columns_slab.restype = i
+    L.demag_rows_inverse.argtypes = [vp, vp, i, i, d, vp, vp]
+    L.demag_rows_inverse.restype = i
     L.demag_tensor_points.argtypes = [i, vp, vp, vp]
     L.demag_tensor_points.restype = i
     L.demag_plan_set_path.argtypes = [vp, i]
@@ -317,6 +325,58 @@ def demag_plan_compress(plan, tol):
     return int(n.value)
 
 
+def demag_plan_keep_slab(plan, k0, k1):
+    """Keep only the x-frequencies k0 <= kx < k1 of the plan's tensor
+    (demag_plan_keep_slab in demag.h)."""
+    _check(lib().demag_plan_keep_slab(ctypes.c_void_p(plan), int(k0), int(k1)), "demag_plan_keep_slab")
+
+
+def _spectrum_check(t, info, shape, name):
+    import torch
+    want = torch.complex128 if info["precision"] == PREC_FP64 else torch.complex64
+    if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous CUDA %s tensor" % (name, want))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+
+
+def _planes_check(t, info, p1, name):
+    B = _field_check(t, info, name)
+    if p1 > B * info["L"] * 3:
+        raise ValueError("plane range beyond the %d planes of %s" % (B * info["L"] * 3, name))
+
+
+def demag_rows_forward(plan, m, p0, p1, spec, stream=None, info=None):
+    """spec [p1 - p0, Kx, ny] (complex) <- row spectra of planes p0..p1-1 of m."""
+    info = info or demag_plan_info(plan)
+    _planes_check(m, info, p1, "m")
+    _spectrum_check(spec, info, (p1 - p0, info["Px"] // 2 + 1, info["ny"]), "spec")
+    _check(lib().demag_rows_forward(ctypes.c_void_p(plan), ctypes.c_void_p(m.data_ptr()), int(p0), int(p1),
+                                    ctypes.c_void_p(spec.data_ptr()), _stream(stream)), "demag_rows_forward")
+    return spec
+
+
+def demag_columns_slab(plan, spec, k0, k1, B, stream=None, info=None):
+    """Column steps of every plane of B states at k0 <= kx < k1, in place on
+    spec [B * L * 3, k1 - k0, ny] (complex)."""
+    info = info or demag_plan_info(plan)
+    _spectrum_check(spec, info, (B * info["L"] * 3, k1 - k0, info["ny"]), "spec")
+    _check(lib().demag_columns_slab(ctypes.c_void_p(plan), ctypes.c_void_p(spec.data_ptr()), int(k0), int(k1),
+                                    int(B), _stream(stream)), "demag_columns_slab")
+    return spec
+
+
+def demag_rows_inverse(plan, spec, p0, p1, Ms, H, stream=None, info=None):
+    """Planes p0..p1-1 of H <- inverse row transforms of spec [p1 - p0, Kx, ny]."""
+    info = info or demag_plan_info(plan)
+    _planes_check(H, info, p1, "H")
+    _spectrum_check(spec, info, (p1 - p0, info["Px"] // 2 + 1, info["ny"]), "spec")
+    _check(lib().demag_rows_inverse(ctypes.c_void_p(plan), ctypes.c_void_p(spec.data_ptr()), int(p0), int(p1),
+                                    float(Ms), ctypes.c_void_p(H.data_ptr()), _stream(stream)),
+           "demag_rows_inverse")
+    return H
+
+
 def demag_tensor_points(geom, out, stream=None):
     """geom: CUDA float64 [n, 9]; out: CUDA float64 [n, 6]."""
     import torch
@@ -442,6 +502,7 @@ class Plan:
     def __init__(self, nx, ny, dx, dy, thickness, precision=PREC_FP32, max_batch=1, stream=None):
         self.handle = demag_plan_create(nx, ny, dx, dy, thickness, precision, max_batch, stream)
         self.info = demag_plan_info(self.handle)
+        self.slab = None
 
     @property
     def dtype(self):
@@ -461,6 +522,7 @@ class Plan:
         self = cls.__new__(cls)
         self.handle = demag_plan_create_equidistant(nx, ny, nz, dx, dy, dz, precision, max_batch, stream)
         self.info = demag_plan_info(self.handle)
+        self.slab = None
         return self
 
     def compress(self, tol):
@@ -469,6 +531,12 @@ class Plan:
         n = demag_plan_compress(self.handle, tol)
         self.info = demag_plan_info(self.handle)
         return n
+
+    def keep_slab(self, k0, k1):
+        """Keep only the x-frequencies k0 <= kx < k1 of the tensor; the plan
+        then runs the sharded steps only (demag_plan_keep_slab)."""
+        demag_plan_keep_slab(self.handle, k0, k1)
+        self.slab = (int(k0), int(k1))
 
     def close(self):
         if self.handle:

@@ -543,6 +543,8 @@ static demag_status check_apply(demag_plan_t plan, const void *m, double Ms, con
     if (m == H) return fail(DEMAG_EINVAL, "H must not alias m");
     if (B < 1 || B > plan->max_batch) return fail(DEMAG_EINVAL, "B must be in [1, max_batch]");
     if (!std::isfinite(Ms)) return fail(DEMAG_EINVAL, "Ms must be finite");
+    if (plan->slab_k1 >= 0)
+        return fail(DEMAG_EUNSUPPORTED, "the plan keeps one kx slab of its tensor: it runs demag_columns_slab only");
     return DEMAG_OK;
 }
 
@@ -868,6 +870,7 @@ demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_b
     if (!plan->umajor || plan->method != 0 || (plan->contract_mode != 3 && plan->contract_mode != 4))
         return fail(DEMAG_EUNSUPPORTED, "compression needs a split-precision plan on path 6 or 7");
     if (plan->d_bmask) return fail(DEMAG_EUNSUPPORTED, "the plan's tensor is already compressed");
+    if (plan->slab_k1 >= 0) return fail(DEMAG_EUNSUPPORTED, "the plan keeps one kx slab of its tensor");
     DEMAG_CUDA(cudaDeviceSynchronize());  // no apply may be reading the tensor
     float *out = nullptr;
     size_t bytes = 0;
@@ -883,6 +886,105 @@ demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_b
     plan->d_bfirst = first;
     plan->compress_tol = tol;
     if (stored_bytes) *stored_bytes = bytes;
+    return DEMAG_OK;
+}
+
+// Bytes of the stored tensor per x-frequency (every layout is kx-major).
+static size_t tensor_kx_bytes(const demag_plan *p) {
+    const size_t real = p->precision == DEMAG_PREC_FP64 ? 8 : 4;
+    return p->umajor ? (size_t)p->Qy * ub_entry(p->L) * real : (size_t)p->npairs * 6 * p->QyS * real;
+}
+
+demag_status demag_plan_keep_slab(demag_plan_t plan, int k0, int k1) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    if (plan->method != 0 || !plan->split)
+        return fail(DEMAG_EUNSUPPORTED, "slabs need a hybrid plan on the split path (paths 2, 3, 4, 6, 7)");
+    if (plan->d_bmask) return fail(DEMAG_EUNSUPPORTED, "the plan's tensor is compressed");
+    if (plan->slab_k1 >= 0) return fail(DEMAG_EUNSUPPORTED, "the plan already keeps a slab");
+    if (k0 < 0 || k1 <= k0 || k1 > plan->Kx)
+        return fail(DEMAG_EINVAL, "need 0 <= k0 < k1 <= Px / 2 + 1 = " + std::to_string(plan->Kx));
+    DEMAG_CUDA(cudaDeviceSynchronize());  // no apply may be reading the tensor
+    const size_t kb = tensor_kx_bytes(plan), bytes = (size_t)(k1 - k0) * kb;
+    void *slab = nullptr;
+    DEMAG_TRY(dalloc(&slab, bytes, "tensor slab"));
+    cudaError_t e = cudaMemcpy(slab, (const char *)plan->d_tensor + (size_t)k0 * kb, bytes, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(slab);
+        return cuda_fail(e, "tensor slab copy");
+    }
+    cudaFree(plan->d_tensor);
+    plan->d_tensor = slab;
+    plan->tensor_bytes = bytes;
+    plan->slab_k0 = k0;
+    plan->slab_k1 = k1;
+    // the row spectrum workspace serves demag_apply only; the column
+    // workspace shrinks to the slab
+    cudaFree(plan->d_spec);
+    plan->d_spec = nullptr;
+    const bool fp64 = plan->precision == DEMAG_PREC_FP64;
+    const size_t w2 = split_workspace_bytes(plan->L, plan->max_batch, plan->log2Px, plan->log2Py, fp64) /
+                      plan->Kx * (k1 - k0);
+    cudaFree(plan->d_spec2);
+    plan->d_spec2 = nullptr;
+    DEMAG_TRY(dalloc(&plan->d_spec2, w2, "column workspace"));
+    return DEMAG_OK;
+}
+
+static demag_status check_planes(demag_plan_t plan, const void *a, const void *b, int p0, int p1) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    if (!a || !b) return fail(DEMAG_EINVAL, "a field or spectrum pointer is NULL");
+    const int P = plan->max_batch * plan->L * 3;
+    if (p0 < 0 || p1 <= p0 || p1 > P)
+        return fail(DEMAG_EINVAL, "need 0 <= p0 < p1 <= max_batch * L * 3 = " + std::to_string(P));
+    return DEMAG_OK;
+}
+
+demag_status demag_rows_forward(demag_plan_t plan, const void *m, int p0, int p1, void *spec, void *stream) {
+    DEMAG_TRY(check_planes(plan, m, spec, p0, p1));
+    const bool fp64 = plan->precision == DEMAG_PREC_FP64;
+    const size_t real = fp64 ? 8 : 4;
+    ApplyArgs a = apply_args(plan, 0.0, plan->max_batch);
+    a.spec = spec;
+    a.planes = p1 - p0;
+    const char *mp = (const char *)m + (size_t)p0 * plan->nx * plan->ny * real;
+    cudaError_t e = launch_apply_stage(a, 0, mp, nullptr, fp64, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "row transform kernels");
+    return DEMAG_OK;
+}
+
+demag_status demag_rows_inverse(demag_plan_t plan, const void *spec, int p0, int p1, double Ms, void *H,
+                                void *stream) {
+    DEMAG_TRY(check_planes(plan, spec, H, p0, p1));
+    if (!std::isfinite(Ms)) return fail(DEMAG_EINVAL, "Ms must be finite");
+    const bool fp64 = plan->precision == DEMAG_PREC_FP64;
+    const size_t real = fp64 ? 8 : 4;
+    ApplyArgs a = apply_args(plan, Ms, plan->max_batch);
+    a.spec = const_cast<void *>(spec);
+    a.planes = p1 - p0;
+    char *hp = (char *)H + (size_t)p0 * plan->nx * plan->ny * real;
+    cudaError_t e = launch_apply_stage(a, 2, nullptr, hp, fp64, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "row transform kernels");
+    return DEMAG_OK;
+}
+
+demag_status demag_columns_slab(demag_plan_t plan, void *spec, int k0, int k1, int B, void *stream) {
+    if (!plan) return fail(DEMAG_EINVAL, "plan is NULL");
+    if (!spec) return fail(DEMAG_EINVAL, "spec is NULL");
+    if (plan->method != 0 || !plan->split)
+        return fail(DEMAG_EUNSUPPORTED, "slabs need a hybrid plan on the split path (paths 2, 3, 4, 6, 7)");
+    if (plan->d_bmask) return fail(DEMAG_EUNSUPPORTED, "the plan's tensor is compressed");
+    if (B < 1 || B > plan->max_batch) return fail(DEMAG_EINVAL, "B must be in [1, max_batch]");
+    const int s0 = plan->slab_k1 >= 0 ? plan->slab_k0 : 0, s1 = plan->slab_k1 >= 0 ? plan->slab_k1 : plan->Kx;
+    if (k0 < s0 || k1 <= k0 || k1 > s1)
+        return fail(DEMAG_EINVAL, "need " + std::to_string(s0) + " <= k0 < k1 <= " + std::to_string(s1) +
+                                      " (the x-frequencies of the plan's tensor)");
+    ApplyArgs a = apply_args(plan, 0.0, B);
+    a.spec = spec;
+    a.kx_count = k1 - k0;
+    a.tensor = (const char *)plan->d_tensor + (size_t)(k0 - s0) * tensor_kx_bytes(plan);
+    cudaError_t e = launch_apply_stage(a, 1, nullptr, nullptr, plan->precision == DEMAG_PREC_FP64,
+                                       (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "column and contraction kernels");
     return DEMAG_OK;
 }
 

@@ -326,7 +326,7 @@ template <typename T>
 static cudaError_t rows_stage(const ApplyArgs &a, const T *m, T *H, bool forward, cudaStream_t st) {
     using C = typename cpx_of<T>::type;
     const int Px = 1 << a.log2Px;
-    const int planes = a.B * a.L * 3;
+    const int planes = a.planes ? a.planes : a.B * a.L * 3;
     const int npair = row_pairs<T>(a.log2Px);
     const int chunks = (a.ny + 2 * npair - 1) / (2 * npair);
     const size_t smem_rows = (size_t)npair * (Px + 1) * sizeof(C);

@@ -871,7 +871,7 @@ template <typename T>
 cudaError_t launch_rows512(const ApplyArgs &a, const void *m, void *H, bool forward, cudaStream_t st) {
     using C = typename cpx_of<T>::type;
     const size_t smem = (size_t)8 * kColRow * sizeof(C);
-    const dim3 grid((a.ny + 15) / 16, a.B * a.L * 3);
+    const dim3 grid((a.ny + 15) / 16, a.planes ? a.planes : a.B * a.L * 3);
     cudaError_t e;
     if (forward) {
         if ((e = cudaFuncSetAttribute(k_rows_forward8<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

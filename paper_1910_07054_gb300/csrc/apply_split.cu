@@ -256,7 +256,7 @@ template <typename T>
 static cudaError_t split_columns(const ApplyArgs &a, cudaStream_t st, cudaEvent_t *ev) {
     using C = typename cpx_of<T>::type;
     const int Py = 1 << a.log2Py;
-    const int Kx = (1 << a.log2Px) / 2 + 1;
+    const int Kx = a.kx_count ? a.kx_count : (1 << a.log2Px) / 2 + 1;
     const int planes = a.B * 3 * a.L;
     int G = 16;  // planes per column block: at most ~72 KB, so that 3 blocks share an SM
     while (G > 1 && (size_t)G * (Py + 1) * sizeof(C) > 72 * 1024) G /= 2;

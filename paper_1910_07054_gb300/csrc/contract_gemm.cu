@@ -480,7 +480,7 @@ size_t tc_smem_bytes(int L, int npairs) {
 namespace demag {
 
 cudaError_t launch_contract_gemm(const ApplyArgs &a, bool tensor_cores, cudaStream_t st) {
-    const int Py = 1 << a.log2Py, Qy = Py / 2 + 1, Kx = (1 << a.log2Px) / 2 + 1;
+    const int Py = 1 << a.log2Py, Qy = Py / 2 + 1, Kx = a.kx_count ? a.kx_count : (1 << a.log2Px) / 2 + 1;
     const size_t smem = gemm_smem_bytes(a.L, a.B);
     cudaError_t e;
     dim3 grid(Kx, Qy);

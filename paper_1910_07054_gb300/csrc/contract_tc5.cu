@@ -188,7 +188,7 @@ template <bool BF, bool CMP>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restrict__ spec2,
                                                                const float *__restrict__ tensor_um,
                                                                const float *__restrict__ ratio, int L, int B,
-                                                               int log2Px, int log2Py, int npairs,
+                                                               int Kx, int log2Py, int npairs,
                                                                const unsigned long long *__restrict__ bmask,
                                                                const unsigned *__restrict__ bfirst) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
     constexpr int KC = TcKC<BF>::value;  // K columns per chunk
     constexpr int PW = Split<BF>::kPerWord;
     const TcShape sh = tc_shape(L, B, npairs, KC);
-    const int Py = 1 << log2Py, Qy = Py / 2 + 1, Kx = (1 << log2Px) / 2 + 1;
+    const int Py = 1 << log2Py, Qy = Py / 2 + 1;
     const int nent = Kx * Qy;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Lp = sh.Lp, planes = sh.planes, R = sh.R;
@@ -626,10 +626,11 @@ cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st) 
     int dev = 0, nsm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int nent = ((1 << a.log2Px) / 2 + 1) * ((1 << a.log2Py) / 2 + 1);
+    const int Kx = a.kx_count ? a.kx_count : (1 << a.log2Px) / 2 + 1;
+    const int nent = Kx * ((1 << a.log2Py) / 2 + 1);
     const int grid = nent < nsm ? nent : nsm;
     kernel<<<grid, kTcThreads, sh.total, st>>>((float2 *)a.spec2, (const float *)a.tensor, (const float *)a.ratio,
-                                               a.L, a.B, a.log2Px, a.log2Py, a.npairs, a.bmask, a.bfirst);
+                                               a.L, a.B, Kx, a.log2Py, a.npairs, a.bmask, a.bfirst);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,8 @@ struct ApplyArgs {
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
     const void *twz = nullptr;        // equidistant plans: twiddles for Pz
     int log2Pz = 0;                   // equidistant plans: padded z size
+    int planes = 0;                   // row transforms: planes to transform (0: B * L * 3)
+    int kx_count = 0;                 // split path: x-frequencies in spec, spec2 and tensor (0: all)
     double Ms;
 };
 
@@ -182,6 +184,7 @@ struct demag_plan {
     unsigned long long *d_bmask = nullptr;  // after demag_plan_compress: kept blocks per entry
     unsigned *d_bfirst = nullptr;           // and each entry's first block
     double compress_tol = -1.0;             // < 0: not compressed
+    int slab_k0 = 0, slab_k1 = -1;          // after demag_plan_keep_slab: the x-frequencies kept (k1 < 0: all)
     int natural = 0;              // fused 512-point column kernel, natural folded-ky tensor
     int method = 0;               // 0 hybrid (Eq. FFT_v2), 1 equidistant 3D FFT (Eq. FFT_3D)
     int log2Pz = 0;               // equidistant plans: padded z size

@@ -17,9 +17,10 @@ row transforms of its planes.  The exchanges land in local memory (no remote
 loads, no multicast): 2 x the row spectrum per apply in total.
 
 This module holds the partitioning and the two exchanges.  The three local
-steps are passed in as callables (on a GPU: the library's row and slab kernels;
-the CPU tests pass stand-ins), so the orchestration runs unchanged over NCCL or
-gloo process groups.
+steps are passed in as callables (on a GPU: `gpu_steps`, the library's row and
+slab kernels through demag_rows_forward, demag_columns_slab and
+demag_rows_inverse; the CPU tests pass stand-ins), so the orchestration runs
+unchanged over NCCL or gloo process groups.
 """
 
 
@@ -55,13 +56,15 @@ class ShardedApply:
     None for one rank).
     """
 
-    def __init__(self, P, Kx, ny, rank, world, rows_forward, columns_slab, rows_inverse, dist=None):
+    def __init__(self, P, Kx, ny, rank, world, rows_forward, columns_slab, rows_inverse, dist=None,
+                 stage_host=False):
         self.P, self.Kx, self.ny = P, Kx, ny
         self.rank, self.world = rank, world
         self.planes = even_ranges(P, world)
         self.slabs = even_ranges(Kx, world)
         self.rows_forward, self.columns_slab, self.rows_inverse = rows_forward, columns_slab, rows_inverse
         self.dist = dist
+        self.stage_host = stage_host  # exchange through host memory (gloo ranks with device spectra)
 
     def bytes_exchanged(self, itemsize):
         """Bytes this rank sends per apply (both exchanges), complex items of `itemsize`."""
@@ -78,10 +81,14 @@ class ShardedApply:
         if self.world == 1:
             return [send_blocks[0]]
         send = torch.cat([torch.view_as_real(b.contiguous()).reshape(-1) for b in send_blocks])
+        home = send.device
+        if self.stage_host:
+            send = send.cpu()
         in_sizes = [2 * b.numel() for b in send_blocks]
         out_sizes = [2 * int(torch.Size(s).numel()) for s in recv_shapes]
         recv = torch.empty(sum(out_sizes), dtype=send.dtype, device=send.device)
         self.dist.all_to_all_single(recv, send, out_sizes, in_sizes)
+        recv = recv.to(home)
         out, o = [], 0
         for s, n in zip(recv_shapes, out_sizes):
             out.append(torch.view_as_complex(recv[o:o + n].view(*s, 2)))
@@ -107,3 +114,30 @@ class ShardedApply:
             spec[:, a:b, :] = blk
         self.rows_inverse(spec, p0, p1)
         return spec
+
+
+def gpu_steps(plan, m, H, B, Ms, k0, k1, stream=None):
+    """The three local steps of a ShardedApply on the library's kernels.
+
+    plan: a ._lib.Plan on the split path whose tensor covers x-frequencies
+    k0..k1-1 (this rank's slab; after Plan.keep_slab(k0, k1) it holds nothing
+    else); m, H: the batch's device fields [B, L, 3, ny, nx] (this rank reads
+    and writes only its planes of them).  Returns (rows_forward, columns_slab,
+    rows_inverse) for ShardedApply."""
+    import torch
+    from . import _lib
+    info = plan.info
+    Kx, ny = info["Px"] // 2 + 1, info["ny"]
+    cdt = torch.complex128 if info["precision"] == _lib.PREC_FP64 else torch.complex64
+
+    def rows_forward(p0, p1):
+        spec = torch.empty(p1 - p0, Kx, ny, dtype=cdt, device=m.device)
+        return _lib.demag_rows_forward(plan.handle, m, p0, p1, spec, stream, info)
+
+    def columns_slab(slab):
+        _lib.demag_columns_slab(plan.handle, slab, k0, k1, B, stream, info)
+
+    def rows_inverse(spec, p0, p1):
+        _lib.demag_rows_inverse(plan.handle, spec, p0, p1, Ms, H, stream, info)
+
+    return rows_forward, columns_slab, rows_inverse

@@ -63,6 +63,10 @@ def test_other_entry_points_reject_null_and_bad_sizes():
     assert lib.demag_plan_info(None, None) == 1
     assert lib.demag_plan_tensor(None, None, 0, None) == 1
     assert lib.demag_plan_compress(None, 1e-8, None) == 1
+    assert lib.demag_plan_keep_slab(None, 0, 1) == 1
+    assert lib.demag_rows_forward(None, None, 0, 1, None, None) == 1
+    assert lib.demag_rows_inverse(None, None, 0, 1, 1.0, None, None) == 1
+    assert lib.demag_columns_slab(None, None, 0, 1, 1, None) == 1
     assert lib.demag_destroy(None) == 0
 
 
