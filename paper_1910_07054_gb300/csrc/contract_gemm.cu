@@ -119,14 +119,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int e = 4 * e4 + w;
-                const int c = e / NR, q = e - c * NR;  // [component][block][row][column]
+                const int c = e / NR, q = e - c * NR;  // [component][block][row slot][column]
                 // block (R, C) of index q / 64: block rows of nb, nb - 1, ... blocks
                 int R = 0, rem = q >> 6;
                 while (rem >= nb - R) {
                     rem -= nb - R;
                     ++R;
                 }
-                const int a = 8 * R + ((q >> 3) & 7), b = 8 * (R + rem) + (q & 7);
+                // row slot s of block (R, C) holds row s ^ (C mod 8) (ub_at)
+                const int a = 8 * R + (((q >> 3) ^ (R + rem)) & 7), b = 8 * (R + rem) + (q & 7);
                 if (a >= L || b >= L) continue;  // padding layers
                 // value M(a, b) = (t_a / t_0) N(a <- b): target a <- source b
                 Kd[(c * Lp + a) * S + b] = ratio[a * L] * vals[w];
@@ -399,8 +400,8 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_contract_tc(float2 *__restr
                 const int i = mt * 16 + gr + ((f & 1) ? 8 : 0), jj = k0 + gc + ((f & 2) ? 4 : 0);
                 const int I = i >> 3, J = jj >> 3;
                 rev[f] = I > J;
-                base[f] = (i < L && jj < L) ? (rev[f] ? ub_blk(J, I, nb) + 8 * (jj & 7) + (i & 7)
-                                                      : ub_blk(I, J, nb) + 8 * (i & 7) + (jj & 7))
+                base[f] = (i < L && jj < L) ? (rev[f] ? ub_blk(J, I, nb) + ub_at(jj & 7, i & 7, I)
+                                                      : ub_blk(I, J, nb) + ub_at(i & 7, jj & 7, J))
                                             : -1;
                 scl[f] = s_itau[i];
             }

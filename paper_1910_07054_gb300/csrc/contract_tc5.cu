@@ -79,7 +79,7 @@ struct TcShape {
     size_t raw_bytes, rows_bytes, in_bytes, s_bytes, stage_bytes, off_stage, total;
 };
 
-__host__ __device__ inline size_t round128(size_t v) { return (v + 127) / 128 * 128; }
+__host__ __device__ inline size_t round256(size_t v) { return (v + 255) / 256 * 256; }
 
 __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs, int kc = 16) {
     TcShape s;
@@ -94,9 +94,9 @@ __host__ __device__ inline TcShape tc_shape(int L, int B, int npairs, int kc = 1
     // a state's 3L complex values, padded so that consecutive states start 16
     // bytes apart modulo 128 (the 8 states a warp reads at once hit 8 bank groups)
     s.seg = 3 * L + ((2 - (3 * L) % 16) + 16) % 16;
-    s.raw_bytes = round128((size_t)s.NB * 4 + 256);  // + a zero block for dropped blocks of compressed tensors
-    s.rows_bytes = round128((size_t)2 * B * s.seg * 8);
-    s.in_bytes = s.raw_bytes + s.rows_bytes;  // one input buffer (two of them)
+    s.raw_bytes = round256((size_t)s.NB * 4 + 256);  // + a zero block for dropped blocks of compressed tensors
+    s.rows_bytes = round256((size_t)2 * B * s.seg * 8);
+    s.in_bytes = s.raw_bytes + s.rows_bytes;  // one input buffer (two of them): tensor blocks start on 256 bytes
     s.s_bytes = (size_t)kTcN * 64;  // N rows x 64 bytes of K
     s.stage_bytes = 2 * s.s_bytes;            // S hi, S lo
     s.off_stage = 2 * s.in_bytes;
@@ -429,19 +429,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                                 off = bo >= 0 ? off + bo : inb + (int)sh.raw_bytes - 256;
                             }
                             if (I <= J) {
-                                // row i8 of block (I, J): 8 consecutive values
+                                // row i8 of block (I, J): 8 consecutive values (row
+                                // slot i8 ^ (J mod 8), layout.cuh)
                                 const float4 *src = reinterpret_cast<const float4 *>(
-                                    smem + off + (CMP ? 0 : 4 * ub_blk(I, J, nb)) + 32 * i8);
+                                    smem + off + (CMP ? 0 : 4 * ub_blk(I, J, nb)) + 32 * (i8 ^ (J & 7)));
                                 const float4 x0 = src[0], x1 = src[1];
                                 vs8[0] = x0.x, vs8[1] = x0.y, vs8[2] = x0.z, vs8[3] = x0.w;
                                 vs8[4] = x1.x, vs8[5] = x1.y, vs8[6] = x1.z, vs8[7] = x1.w;
                                 sg = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
                             } else {
-                                // column i8 of block (J, I): M(i, 8 J + e) = s_c M(8 J + e, i)
-                                const float *src = reinterpret_cast<const float *>(
-                                    smem + off + (CMP ? 0 : 4 * ub_blk(J, I, nb)) + 4 * i8);
+                                // column i8 of block (J, I): M(i, 8 J + e) = s_c M(8 J + e, i),
+                                // row e in slot e ^ (I mod 8) (layout.cuh).  Blocks start on
+                                // 256 bytes, so the slot is bits 5-7 of the offset: one XOR
+                                // per value
+                                const unsigned a0 =
+                                    (unsigned)(off + (CMP ? 0 : 4 * ub_blk(J, I, nb)) + 4 * i8) ^ (32u * (unsigned)(I & 7));
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) vs8[e] = src[8 * e];
+                                for (int e = 0; e < 8; ++e)
+                                    vs8[e] = *reinterpret_cast<const float *>(smem + (a0 ^ (32u * (unsigned)e)));
                                 sg = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
                             }
 #pragma unroll

@@ -1068,10 +1068,10 @@ __global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npai
         const double v[6] = {A.x * f, A.y * f, Bp.x * f, Bp.y * f, Cc.y * f, -Cc.x * f};
         T *o = tensor + ((size_t)kx * Qy + u) * (6 * (size_t)rl);
         const int I = i >> 3, J = j >> 3;
-        const int e1 = ub_blk(I, J, nb) + 8 * (i & 7) + (j & 7);
+        const int e1 = ub_blk(I, J, nb) + ub_at(i & 7, j & 7, J);
         for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e1] = (T)v[c];
         if (I == J && i != j) {
-            const int e2 = ub_blk(I, I, nb) + 8 * (j & 7) + (i & 7);
+            const int e2 = ub_blk(I, I, nb) + ub_at(j & 7, i & 7, I);
             for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e2] = (T)(c >= 4 ? -v[c] : v[c]);
         }
         return;

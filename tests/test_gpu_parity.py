@@ -320,7 +320,8 @@ def test_gpu_argument_errors():
 def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
     """A dense-product plan's stored tensor, decoded here from the documented
     blocked layout (8 x 8 layer blocks R <= C of M(i, j) = (t_i / t_0) N(i <- j),
-    diagonal blocks mirrored with xz and yz negated, layers past L zero), equals
+    row a of block (R, C) in row slot a ^ (C mod 8), diagonal blocks mirrored
+    with xz and yz negated, layers past L zero), equals
     the oracle's transformed kernels.  10 layers cross a block boundary."""
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=1)
     info = plan.info
@@ -355,7 +356,7 @@ def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
                     i, j = 8 * Rb + a, 8 * Cb + b
                     if i >= L or j >= L:
                         continue
-                    e = 64 * blk + 8 * a + b
+                    e = 64 * blk + 8 * (a ^ (Cb & 7)) + b  # rows swizzled by the block column
                     if i <= j:
                         exp[:, :, :, e] = th[i] / th[0] * ref[i, j]
                     else:  # lower half of a diagonal block
