@@ -381,9 +381,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
         }
         // S unit of this thread: (position pq, state b, core column k4)
         constexpr int KG = 4;  // core matrices (16 bytes of K) per S row and chunk
+        // (lanes 8 g .. 8 g + 7 of a warp take states 0..7 or 8..15 of one core
+        // column: a quarter-warp's 16-byte stores fill the 128 bytes of eight
+        // core-matrix rows, one bank group each)
         const int sv = lane + 32 * sidx;
         const bool sact = !isA && sv < 2 * kTcBp * KG;
-        const int k4 = sv & (KG - 1), sb = (sv >> 2) & (kTcBp - 1), spq = (sv >> 6) & 1;
+        const int k4 = (sv >> 3) & (KG - 1), sb = (sv & 7) | (((sv >> 5) & 1) << 3), spq = (sv >> 6) & 1;
         const int sn = 32 * spq + sb;  // real column of S; the imaginary one is sn + 16
         const int soff_r = (((sn >> 3) * KG + k4) * 32 + (sn & 7) * 4) * 4;
         const int soff_i = soff_r + 2 * KG * 32 * 4;  // 16 rows = two 8-row groups further
