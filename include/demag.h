@@ -479,10 +479,11 @@ demag_status demag_rows_inverse(demag_plan_t plan, const void *spec, int p0, int
  * with nb = ceil(L/8) layer blocks and NB = 6 * 64 * nb (nb + 1) / 2: each
  * component row holds the 8 x 8 blocks (R <= C) of M(i, j) = (t_i / t_0)
  * N(i <- j), block row by block row, element (i mod 8, j mod 8) of block
- * (R, C) = (i / 8, j / 8) at float 8 ((i mod 8) XOR (C mod 8)) + (j mod 8)
- * of the block (rows swizzled by the block column, which spreads the
- * contraction's column reads over the shared-memory banks); a diagonal block
- * holds both triangles, M(i, j) for i > j
+ * (R, C) = (i / 8, j / 8) at float 32 h + 4 (a XOR (C mod 4) XOR 4 h) + (b mod
+ * 4) of the block, a = i mod 8, b = j mod 8, h = b / 4 (the block's left
+ * half-rows, then its right half-rows, in an order that spreads the
+ * contraction's row and column reads over the shared-memory banks); a
+ * diagonal block holds both triangles, M(i, j) for i > j
  * being M(j, i) with the xz and yz components negated; layers past L zero)
  * with pair (i <= j) numbered row by row
  * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components

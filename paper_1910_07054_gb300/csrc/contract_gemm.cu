@@ -119,15 +119,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_contract_gemm(
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const int e = 4 * e4 + w;
-                const int c = e / NR, q = e - c * NR;  // [component][block][row slot][column]
+                const int c = e / NR, q = e - c * NR;  // [component][block][half-row slots]
                 // block (R, C) of index q / 64: block rows of nb, nb - 1, ... blocks
                 int R = 0, rem = q >> 6;
                 while (rem >= nb - R) {
                     rem -= nb - R;
                     ++R;
                 }
-                // row slot s of block (R, C) holds row s ^ (C mod 8) (ub_at)
-                const int a = 8 * R + (((q >> 3) ^ (R + rem)) & 7), b = 8 * (R + rem) + (q & 7);
+                // float f of block (R, C): half h = f / 32 of row
+                // ((f / 4) mod 8) ^ (C mod 4) ^ 4 h (ub_at)
+                const int f = q & 63, h = f >> 5;
+                const int a = 8 * R + ((((f >> 2) & 7) ^ ((R + rem) & 3) ^ (4 * h))),
+                          b = 8 * (R + rem) + 4 * h + (f & 3);
                 if (a >= L || b >= L) continue;  // padding layers
                 // value M(a, b) = (t_a / t_0) N(a <- b): target a <- source b
                 Kd[(c * Lp + a) * S + b] = ratio[a * L] * vals[w];

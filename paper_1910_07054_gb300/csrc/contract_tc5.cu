@@ -432,24 +432,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                                 off = bo >= 0 ? off + bo : inb + (int)sh.raw_bytes - 256;
                             }
                             if (I <= J) {
-                                // row i8 of block (I, J): 8 consecutive values (row
-                                // slot i8 ^ (J mod 8), layout.cuh)
-                                const float4 *src = reinterpret_cast<const float4 *>(
-                                    smem + off + (CMP ? 0 : 4 * ub_blk(I, J, nb)) + 32 * (i8 ^ (J & 7)));
-                                const float4 x0 = src[0], x1 = src[1];
+                                // row i8 of block (I, J): its two 16-byte halves, slot
+                                // i8 ^ (J mod 4) of the first half-block and that slot
+                                // ^ 4 of the second (layout.cuh; blocks start on 256
+                                // bytes)
+                                const unsigned a0 = (unsigned)(off + (CMP ? 0 : 4 * ub_blk(I, J, nb))) +
+                                                    16u * (unsigned)(i8 ^ (J & 3));
+                                const float4 x0 = *reinterpret_cast<const float4 *>(smem + a0);
+                                const float4 x1 = *reinterpret_cast<const float4 *>(smem + (a0 ^ 0xC0u));
                                 vs8[0] = x0.x, vs8[1] = x0.y, vs8[2] = x0.z, vs8[3] = x0.w;
                                 vs8[4] = x1.x, vs8[5] = x1.y, vs8[6] = x1.z, vs8[7] = x1.w;
                                 sg = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
                             } else {
-                                // column i8 of block (J, I): M(i, 8 J + e) = s_c M(8 J + e, i),
-                                // row e in slot e ^ (I mod 8) (layout.cuh).  Blocks start on
-                                // 256 bytes, so the slot is bits 5-7 of the offset: one XOR
-                                // per value
-                                const unsigned a0 =
-                                    (unsigned)(off + (CMP ? 0 : 4 * ub_blk(J, I, nb)) + 4 * i8) ^ (32u * (unsigned)(I & 7));
+                                // column i8 of block (J, I): M(i, 8 J + e) = s_c M(8 J + e, i).
+                                // Row e's half holding it is slot e ^ (I mod 4) ^ 4 h of
+                                // half-block h = i8 / 4 (layout.cuh): bits 4-6 of the byte
+                                // offset, so one XOR per value
+                                const int hh = i8 >> 2;
+                                const unsigned a0 = ((unsigned)(off + (CMP ? 0 : 4 * ub_blk(J, I, nb)) + 128 * hh +
+                                                                4 * (i8 & 3))) ^
+                                                    (16u * (unsigned)((I & 3) ^ (4 * hh)));
 #pragma unroll
                                 for (int e = 0; e < 8; ++e)
-                                    vs8[e] = *reinterpret_cast<const float *>(smem + (a0 ^ (32u * (unsigned)e)));
+                                    vs8[e] = *reinterpret_cast<const float *>(smem + (a0 ^ (16u * (unsigned)e)));
                                 sg = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
                             }
 #pragma unroll

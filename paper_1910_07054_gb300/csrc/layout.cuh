@@ -59,9 +59,9 @@ __host__ __device__ inline int tensor_row(int log2Py, bool fp64) {
 // The u-major tensor layout (dense-product plans) holds one (kx, u) entry of
 // 6 component rows.  A component row holds the layer matrix prescaled by the
 // target thickness, M(i, j) = (t_i / t_0) N(i <- j), in 8 x 8 blocks of layers
-// (R, C), R <= C, block row by block row, each block row-major (row i, column
-// j) with its rows swizzled: row a of block (R, C) is stored in row slot
-// a ^ (C mod 8) (ub_at).  Off-diagonal blocks hold pairs i < j; a diagonal block holds both
+// (R, C), R <= C, block row by block row; within a block the left halves
+// (columns 0-3) of the 8 rows come first, then the right halves, each half-row
+// 16 bytes, in a swizzled order (ub_at).  Off-diagonal blocks hold pairs i < j; a diagonal block holds both
 // triangles, the lower one as M(i, j) = s_c M(j, i) with s_c = -1 for xz and
 // yz, +1 otherwise (reciprocity, t_i N(i <- j) = t_j P N(j <- i) P with P =
 // diag(1, 1, -1)).  Layers past L are zero.  For i > j in different blocks
@@ -73,12 +73,16 @@ __host__ __device__ inline int ub_row(int L) { return ub_nb(L) * (ub_nb(L) + 1) 
 __host__ __device__ inline int ub_entry(int L) { return 6 * ub_row(L); }
 // First float of block (R, C), R <= C, in a component row.
 __host__ __device__ inline int ub_blk(int R, int C, int nb) { return (R * nb - R * (R - 1) / 2 + (C - R)) * 64; }
-// Float of element (a, b) (row a, column b) within block (R, C).  The rows are
-// XOR-swizzled by the block column so that the column reads of the tensor-core
-// contraction, which take one column from each of four consecutive blocks
-// (C = 4k .. 4k + 3) of a block row at once, meet four different groups of 8
-// shared-memory banks; the swizzle is a bit field of the byte offset (bits
-// 5-7), so a reader XORs it into the address once per block.
-__host__ __device__ inline int ub_at(int a, int b, int C) { return 8 * (a ^ (C & 7)) + b; }
+// Float of element (a, b) (row a, column b) within block (R, C): half h = b / 4
+// of row a is the 16-byte slot a ^ (C mod 4) ^ 4 h of half-block h.  The
+// tensor-core contraction reads a block two ways, and both meet 32 different
+// banks: 8 lanes reading rows 0..7 of one block, one half-row each (16-byte
+// loads), and 32 lanes reading one value of columns 0..7 of four consecutive
+// blocks (C = 4k .. 4k + 3) of a block row.  The slot is bits 4-6 of the byte
+// offset in a 256-byte block, so a reader XORs it into the address.
+__host__ __device__ inline int ub_at(int a, int b, int C) {
+    const int h = b >> 2;
+    return 32 * h + 4 * (a ^ (C & 3) ^ (4 * h)) + (b & 3);
+}
 
 }  // namespace demag

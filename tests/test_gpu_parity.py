@@ -320,7 +320,8 @@ def test_gpu_argument_errors():
 def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
     """A dense-product plan's stored tensor, decoded here from the documented
     blocked layout (8 x 8 layer blocks R <= C of M(i, j) = (t_i / t_0) N(i <- j),
-    row a of block (R, C) in row slot a ^ (C mod 8), diagonal blocks mirrored
+    half h = b / 4 of row a of block (R, C) in 16-byte slot a ^ (C mod 4) ^ 4 h
+    of half-block h, diagonal blocks mirrored
     with xz and yz negated, layers past L zero), equals
     the oracle's transformed kernels.  10 layers cross a block boundary."""
     plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=1)
@@ -356,7 +357,8 @@ def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
                     i, j = 8 * Rb + a, 8 * Cb + b
                     if i >= L or j >= L:
                         continue
-                    e = 64 * blk + 8 * (a ^ (Cb & 7)) + b  # rows swizzled by the block column
+                    h = b // 4  # half-row h of row a in slot a ^ (Cb mod 4) ^ 4h of half-block h
+                    e = 64 * blk + 32 * h + 4 * (a ^ (Cb & 3) ^ (4 * h)) + (b & 3)
                     if i <= j:
                         exp[:, :, :, e] = th[i] / th[0] * ref[i, j]
                     else:  # lower half of a diagonal block
