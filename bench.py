@@ -548,9 +548,11 @@ def mram_block(args, world, rank, dist, peaks, with_oracle):
 
 def batched_measurement(steps, peaks, n=512, layers=64, paths=(6, 7, 4, 3)):
     """512 x 512 cells (n x n if given), 64 layers, 16 states per apply: the
-    split-precision contraction on the tcgen05 tensor cores (path 6, the plan's
-    default), with warp-level MMAs (path 4) and the same products on the FP32
-    cores (path 3); same plan, same data movement."""
+    split-precision contraction on the tcgen05 tensor cores (path 6, the
+    DEMAG_PREC_SPLIT_TF32 plan's default), with warp-level MMAs (path 4) and the
+    same products on the FP32 cores (path 3), all on one plan; and path 7 on a
+    DEMAG_PREC_SPLIT_BF16 plan (its tensor stored as BF16 split pairs), built
+    when path 7 is asked for.  Same data movement throughout."""
     import numpy as np
     import torch
 
@@ -570,12 +572,20 @@ def batched_measurement(steps, peaks, n=512, layers=64, paths=(6, 7, 4, 3)):
            "plan_create_s": build_s}
     fields = {}
     names = {4: "tensor_cores_3xtf32", 6: "tcgen05_3xtf32", 7: "tcgen05_3xbf16", 3: "fp32_cores"}
+    plan_bf16 = None
     for path in paths:
         name = names[path]
-        dm.demag_plan_set_path(plan.handle, path)
-        info = dm.demag_plan_info(plan.handle)
-        dm.demag_apply(plan.handle, m, inputs.MS_DEFAULT, H, info=info)
-        st = np.mean([dm.demag_apply_timed(plan.handle, m, inputs.MS_DEFAULT, H, info=info)
+        if path == 7:
+            if plan_bf16 is None:
+                plan_bf16 = dm.Plan(nx, ny, c["dx"], c["dy"], th, precision=dm.PREC_SPLIT_BF16, max_batch=B)
+            use = plan_bf16
+        else:
+            use = plan
+            dm.demag_plan_set_path(use.handle, path)
+        info = dm.demag_plan_info(use.handle)
+        assert info["path"] == path
+        dm.demag_apply(use.handle, m, inputs.MS_DEFAULT, H, info=info)
+        st = np.mean([dm.demag_apply_timed(use.handle, m, inputs.MS_DEFAULT, H, info=info)
                       for _ in range(steps)], axis=0)
         total = float(st[0] + st[1] + st[2])
         fields[path] = H.clone()
@@ -609,6 +619,8 @@ def batched_measurement(steps, peaks, n=512, layers=64, paths=(6, 7, 4, 3)):
             out["speedup_tcgen05_vs_fp32_cores"] = out["fp32_cores"]["ms_per_apply"] / \
                 out["tcgen05_3xtf32"]["ms_per_apply"]
     plan.close()
+    if plan_bf16 is not None:
+        plan_bf16.close()
     return out
 
 

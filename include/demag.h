@@ -225,7 +225,12 @@ demag_status demag_apply(demag_plan_t plan, const void *m, double Ms, void *H, i
  *           tensor memory, accumulators in tensor memory, one persistent
  *           block per SM.
  *   path 7: (the same plans; the default of DEMAG_PREC_SPLIT_BF16 plans) path
- *           6 with 3xBF16 operands (kind::f16, K = 16 per instruction).
+ *           6 with 3xBF16 operands (kind::f16, K = 16 per instruction).  A
+ *           DEMAG_PREC_SPLIT_BF16 plan that takes path 7 at creation stores
+ *           its tensor already split (see demag_plan_tensor) and runs path 7
+ *           only (DEMAG_EUNSUPPORTED for 3, 4 and 6); a DEMAG_PREC_SPLIT_TF32
+ *           plan on path 7 splits its float tensor in the kernel, with the
+ *           same operands and the same field, bit for bit.
  *   path 0: the default choice of demag_plan_create (5 or 1 when it fits,
  *           else 2; for split-precision plans 6 (TF32) or 7 (BF16) when it
  *           holds the plan, else 4).
@@ -484,7 +489,11 @@ demag_status demag_rows_inverse(demag_plan_t plan, const void *spec, int p0, int
  * half-rows, then its right half-rows, in an order that spreads the
  * contraction's row and column reads over the shared-memory banks); a
  * diagonal block holds both triangles, M(i, j) for i > j
- * being M(j, i) with the xz and yz components negated; layers past L zero)
+ * being M(j, i) with the xz and yz components negated; layers past L zero;
+ * a DEMAG_PREC_SPLIT_BF16 plan on path 7 holds in each 32-bit slot, in place
+ * of the float v, its BF16 split pair hi << 16 | lo, hi = bf16(v), lo = bf16(v
+ * - hi), both rounded to nearest even, with v = -M(i, j) for the zz
+ * component)
  * with pair (i <= j) numbered row by row
  * (i = 0: j = 0..L-1, then i = 1: j = 1..L-1, ...) and components
  * {Re N_xx, Re N_yy, Re N_zz, Re N_xy, Im N_xz, Im N_yz} of the 2D DFT of

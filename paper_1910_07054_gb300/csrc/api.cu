@@ -161,7 +161,8 @@ static demag_status build_tensor(demag_plan *p, cudaStream_t st, int layer, void
             }
     }
     const int npairs = zoffsets ? L : (layer < 0 ? p->npairs : L * L);
-    const int blocked = !zoffsets && layer < 0 ? p->umajor : 0;  // the layout of dense-product plans
+    // the layout of dense-product plans: 1 floats, 2 BF16 split pairs
+    const int blocked = !zoffsets && layer < 0 ? (p->umajor ? (p->packed ? 2 : 1) : 0) : 0;
     std::vector<double> z(L + 1, 0.0);
     for (int l = 0; l < L; ++l) z[l + 1] = z[l] + p->thickness[l];
 
@@ -429,6 +430,8 @@ static demag_status plan_create_impl(demag_plan_t *plan, int nx, int ny, double 
         p->contract_mode = tc5_supported(L, max_batch, p->npairs)
                                ? (precision == DEMAG_PREC_SPLIT_BF16 ? 4 : 3)
                                : 2;
+        // BF16 plans on the tcgen05 kernel store every value pre-split
+        p->packed = p->contract_mode == 4 ? 1 : 0;
     } else {
         p->split = L > fused_max_layers(fp64, p->log2Py) ? 1 : 0;
         p->natural = !p->split && cols512_supported(p->log2Py, L, fp64) ? 1 : 0;
@@ -571,6 +574,7 @@ static ApplyArgs apply_args(demag_plan_t plan, double Ms, int B) {
     a.natural = plan->natural;
     a.bmask = plan->d_bmask;
     a.bfirst = plan->d_bfirst;
+    a.packed = plan->packed;
     a.twz = plan->d_twz;
     a.log2Pz = plan->log2Pz;
     a.Ms = Ms;
@@ -764,6 +768,8 @@ demag_status demag_plan_set_path(demag_plan_t plan, int path) {
     if (plan->umajor) {
         const bool tc5 = tc5_supported(plan->L, plan->max_batch, plan->npairs);
         if (path == 0) path = !tc5 ? 4 : (plan->precision == DEMAG_PREC_SPLIT_BF16 ? 7 : 6);
+        if (plan->packed && path != 7)
+            return fail(DEMAG_EUNSUPPORTED, "a DEMAG_PREC_SPLIT_BF16 plan on the tcgen05 kernel runs path 7 only");
         if (plan->d_bmask && path != 6 && path != 7)
             return fail(DEMAG_EUNSUPPORTED, "a compressed tensor is read by paths 6 and 7 only");
         if (path != 3 && path != 4 && path != 6 && path != 7)
@@ -877,7 +883,8 @@ demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_b
     unsigned long long *mask = nullptr;
     unsigned *first = nullptr;
     const size_t nent = (size_t)plan->Kx * plan->Qy;
-    cudaError_t e = compress_tensor((const float *)plan->d_tensor, nent, plan->L, tol, &out, &bytes, &mask, &first, 0);
+    cudaError_t e = compress_tensor((const float *)plan->d_tensor, nent, plan->L, plan->packed != 0, tol, &out, &bytes,
+                                    &mask, &first, 0);
     if (e != cudaSuccess) return cuda_fail(e, "tensor compression");
     cudaFree(plan->d_tensor);
     plan->d_tensor = out;

@@ -1,4 +1,5 @@
-// Block-sparse compression of a dense-product plan's tensor (layout.cuh).
+// Block-sparse compression of a dense-product plan's tensor (layout.cuh), of
+// floats or of BF16 split pairs.
 //
 // In the in-plane Fourier domain the interaction of two layers decays roughly
 // like exp(-|k| Z) with their distance Z (Sec. 3.2: the cost of the hybrid is
@@ -21,18 +22,27 @@ namespace demag {
 
 namespace {
 
+// |value| of a stored slot: a float, or (packed) a BF16 split pair hi << 16 | lo
+// standing for hi + lo.
+__device__ __forceinline__ float slot_abs(float x, bool packed) {
+    if (!packed) return fabsf(x);
+    const uint32_t w = __float_as_uint(x);
+    return fabsf(__uint_as_float(w & 0xFFFF0000u) + __uint_as_float(w << 16));
+}
+
 // Largest |value| of each component over the whole tensor, as float bits
 // (non-negative floats order like their bit patterns).  Rows are (entry,
 // component); the grid is a multiple of 6 blocks, so each block walks rows of
 // one component and adds one atomic at the end.
 constexpr int kMaxGrid = 6 * 202;
 
-__global__ void k_component_max(const float *__restrict__ t, size_t nent, int row, unsigned *__restrict__ cmax) {
+__global__ void k_component_max(const float *__restrict__ t, size_t nent, int row, bool packed,
+                                unsigned *__restrict__ cmax) {
     __shared__ unsigned part[32];
     unsigned v = 0;
     for (size_t rr = blockIdx.x; rr < nent * 6; rr += gridDim.x) {
         const float *src = t + rr * (size_t)row;
-        for (int i = threadIdx.x; i < row; i += blockDim.x) v = max(v, __float_as_uint(fabsf(src[i])));
+        for (int i = threadIdx.x; i < row; i += blockDim.x) v = max(v, __float_as_uint(slot_abs(src[i], packed)));
     }
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
@@ -45,7 +55,7 @@ __global__ void k_component_max(const float *__restrict__ t, size_t nent, int ro
 
 // One warp per entry: the kept-block mask and count.  A block is kept when any
 // of its 6 x 64 values exceeds tol times its component's maximum.
-__global__ void k_block_mask(const float *__restrict__ t, size_t nent, int row, int nblk,
+__global__ void k_block_mask(const float *__restrict__ t, size_t nent, int row, int nblk, bool packed,
                              const unsigned *__restrict__ cmax, float tol, unsigned long long *__restrict__ mask,
                              int *__restrict__ kept) {
     const size_t e = (size_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -61,7 +71,7 @@ __global__ void k_block_mask(const float *__restrict__ t, size_t nent, int row, 
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const float *blk = te + (size_t)c * row + 64 * b;
-            keep |= fabsf(blk[lane]) > thr[c] || fabsf(blk[lane + 32]) > thr[c];
+            keep |= slot_abs(blk[lane], packed) > thr[c] || slot_abs(blk[lane + 32], packed) > thr[c];
         }
         if (__any_sync(0xffffffffu, keep)) m |= 1ull << b;
     }
@@ -97,8 +107,8 @@ __global__ void k_compact(const float *__restrict__ t, size_t nent, int row, int
 
 }  // namespace
 
-cudaError_t compress_tensor(const float *tensor, size_t nent, int L, double tol, float **out, size_t *out_bytes,
-                            unsigned long long **mask, unsigned **first, cudaStream_t st) {
+cudaError_t compress_tensor(const float *tensor, size_t nent, int L, bool packed, double tol, float **out,
+                            size_t *out_bytes, unsigned long long **mask, unsigned **first, cudaStream_t st) {
     *out = nullptr;
     *mask = nullptr;
     *first = nullptr;
@@ -124,9 +134,9 @@ cudaError_t compress_tensor(const float *tensor, size_t nent, int L, double tol,
     if ((e = cudaMalloc(&d_mask, nent * sizeof(unsigned long long))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&d_first, nent * sizeof(unsigned))) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(d_cmax, 0, 6 * sizeof(unsigned), st)) != cudaSuccess) return fail(e);
-    k_component_max<<<kMaxGrid, 256, 0, st>>>(tensor, nent, row, d_cmax);
+    k_component_max<<<kMaxGrid, 256, 0, st>>>(tensor, nent, row, packed, d_cmax);
     const unsigned wgrid = (unsigned)((nent + 7) / 8);  // 8 warps per block
-    k_block_mask<<<wgrid, 256, 0, st>>>(tensor, nent, row, nblk, d_cmax, (float)tol, d_mask, d_kept);
+    k_block_mask<<<wgrid, 256, 0, st>>>(tensor, nent, row, nblk, packed, d_cmax, (float)tol, d_mask, d_kept);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
     // first block of each entry: exclusive sum of 6 * kept, on the host
     std::vector<int> h_kept(nent);

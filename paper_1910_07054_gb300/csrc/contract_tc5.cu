@@ -184,7 +184,11 @@ __device__ __forceinline__ void tc_mma_chunk(unsigned dt, unsigned at, uint64_t 
 
 // CMP: the plan's tensor is block-compressed (compress.cu): entry e holds its
 // kept blocks only, bmask[e] tells which, bfirst[e] where they start.
-template <bool BF, bool CMP>
+// PK (with BF): the tensor holds each value as its BF16 split pair (hi in the
+// upper half of the 32-bit slot, lo in the lower) and K_zz negated, so the
+// producers only regroup halves into operand words and flip the signs of the
+// reciprocal xz and yz blocks below the diagonal.
+template <bool BF, bool CMP, bool PK>
 __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restrict__ spec2,
                                                                const float *__restrict__ tensor_um,
                                                                const float *__restrict__ ratio, int L, int B,
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
 #pragma unroll
         for (int ci = 0; ci < 3; ++ci) {
             const int comp = tc_comp(co, ci);
-            const float zs = (co == 2 && ci == 2) ? -1.f : 1.f;
+            const float zs = (!PK && co == 2 && ci == 2) ? -1.f : 1.f;  // a packed tensor holds -K_zz
             compc[ci] = comp;
             offc[ci] = comp * NR * 4;
             sup[ci] = zs;
@@ -414,11 +418,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                     // block h of the chunk: K columns KC/2 h .. KC/2 (h + 1) - 1,
                     // PW sub-blocks of 8 (each within one source component, as
                     // Lp is a multiple of 8)
-                    float v[8 * PW];
+                    uint32_t vb[8 * PW];  // the values' bits: floats, or BF16 split pairs (PK)
+                    uint32_t nmask[PW];   // PK: sign bits to flip in the sub-block's words
 #pragma unroll
                     for (int sbk = 0; sbk < PW; ++sbk) {
                         const int kc0 = ch * KC + 8 * PW * h + 8 * sbk;  // first K column of the sub-block
-                        float *vs8 = v + 8 * sbk;
+                        uint32_t *vs8 = vb + 8 * sbk;
+                        nmask[sbk] = 0u;
                         if (kc0 < R) {
                             // the sub-block is layer block J of source component ci
                             const int ci = (kc0 >= Lp) + (kc0 >= 2 * Lp), J = (kc0 - ci * Lp) >> 3;
@@ -438,8 +444,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                                 // bytes)
                                 const unsigned a0 = (unsigned)(off + (CMP ? 0 : 4 * ub_blk(I, J, nb))) +
                                                     16u * (unsigned)(i8 ^ (J & 3));
-                                const float4 x0 = *reinterpret_cast<const float4 *>(smem + a0);
-                                const float4 x1 = *reinterpret_cast<const float4 *>(smem + (a0 ^ 0xC0u));
+                                const uint4 x0 = *reinterpret_cast<const uint4 *>(smem + a0);
+                                const uint4 x1 = *reinterpret_cast<const uint4 *>(smem + (a0 ^ 0xC0u));
                                 vs8[0] = x0.x, vs8[1] = x0.y, vs8[2] = x0.z, vs8[3] = x0.w;
                                 vs8[4] = x1.x, vs8[5] = x1.y, vs8[6] = x1.z, vs8[7] = x1.w;
                                 sg = ci == 0 ? sup[0] : (ci == 1 ? sup[1] : sup[2]);
@@ -454,23 +460,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_contract_tc5(float2 *__restri
                                                     (16u * (unsigned)((I & 3) ^ (4 * hh)));
 #pragma unroll
                                 for (int e = 0; e < 8; ++e)
-                                    vs8[e] = *reinterpret_cast<const float *>(smem + (a0 ^ (16u * (unsigned)e)));
+                                    vs8[e] = *reinterpret_cast<const uint32_t *>(smem + (a0 ^ (16u * (unsigned)e)));
                                 sg = ci == 0 ? slo[0] : (ci == 1 ? slo[1] : slo[2]);
                             }
+                            if constexpr (PK) {
+                                nmask[sbk] = sg < 0.f ? 0x80008000u : 0u;
+                            } else {
 #pragma unroll
-                            for (int e = 0; e < 8; e += 2) {
-                                const float2 y = __fmul2_rn(make_float2(vs8[e], vs8[e + 1]), make_float2(sg, sg));
-                                vs8[e] = y.x;
-                                vs8[e + 1] = y.y;
+                                for (int e = 0; e < 8; e += 2) {
+                                    const float2 y = __fmul2_rn(
+                                        make_float2(__uint_as_float(vs8[e]), __uint_as_float(vs8[e + 1])),
+                                        make_float2(sg, sg));
+                                    vs8[e] = __float_as_uint(y.x);
+                                    vs8[e + 1] = __float_as_uint(y.y);
+                                }
                             }
                         } else {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) vs8[e] = 0.f;
+                            for (int e = 0; e < 8; ++e) vs8[e] = 0u;
                         }
                     }
                     uint32_t hi[8], lo[8];
+                    if constexpr (PK) {
+                        // the stored pairs (hi << 16 | lo) of two consecutive K
+                        // columns give one hi word and one lo word (lower K index in
+                        // the low half); a sign flips both halves of both
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) Split<BF>::word(v + PW * w, hi[w], lo[w]);
+                        for (int w = 0; w < 8; ++w) {
+                            const uint32_t m = nmask[w / 4];
+                            hi[w] = __byte_perm(vb[2 * w], vb[2 * w + 1], 0x7632) ^ m;
+                            lo[w] = __byte_perm(vb[2 * w], vb[2 * w + 1], 0x5410) ^ m;
+                        }
+                    } else {
+                        float v[8 * PW];
+#pragma unroll
+                        for (int k = 0; k < 8 * PW; ++k) v[k] = __uint_as_float(vb[k]);
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) Split<BF>::word(v + PW * w, hi[w], lo[w]);
+                    }
                     const unsigned ta = ta_row + (unsigned)(s * kTcAstage);
                     tc_st8(ta, hi);
                     tc_st8(ta + 16, lo);
@@ -631,8 +658,10 @@ bool tc5_supported(int L, int B, int npairs) {
 cudaError_t launch_contract_tc5(const ApplyArgs &a, bool bf16, cudaStream_t st) {
     const TcShape sh = tc_shape(a.L, a.B, a.npairs, bf16 ? TcKC<true>::value : TcKC<false>::value);
     const bool cmp = a.bmask != nullptr;
-    auto kernel = bf16 ? (cmp ? k_contract_tc5<true, true> : k_contract_tc5<true, false>)
-                       : (cmp ? k_contract_tc5<false, true> : k_contract_tc5<false, false>);
+    if (a.packed && !bf16) return cudaErrorInvalidValue;  // BF16 split pairs feed the BF16 passes only
+    auto kernel = a.packed ? (cmp ? k_contract_tc5<true, true, true> : k_contract_tc5<true, false, true>)
+                  : bf16   ? (cmp ? k_contract_tc5<true, true, false> : k_contract_tc5<true, false, false>)
+                           : (cmp ? k_contract_tc5<false, true, false> : k_contract_tc5<false, false, false>);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.total)) != cudaSuccess)
         return e;

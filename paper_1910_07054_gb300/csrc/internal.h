@@ -96,6 +96,7 @@ struct ApplyArgs {
     const void *out_scale = nullptr;  // optional [L]: H of layer l scaled on output
     const void *twz = nullptr;        // equidistant plans: twiddles for Pz
     int log2Pz = 0;                   // equidistant plans: padded z size
+    int packed = 0;                   // tensor of BF16 split pairs, zz negated (contraction mode 4 only)
     int planes = 0;                   // row transforms: planes to transform (0: B * L * 3)
     int kx_count = 0;                 // split path: x-frequencies in spec, spec2 and tensor (0: all)
     double Ms;
@@ -138,8 +139,9 @@ cudaError_t read_tc_timeouts(unsigned *dst, cudaStream_t st);
 // blocked layout for L layers; blocks whose values are all below tol times their
 // component's maximum are dropped.  On success *out (device, *out_bytes bytes),
 // *mask and *first (device, nent each) are new allocations owned by the caller.
-cudaError_t compress_tensor(const float *tensor, size_t nent, int L, double tol, float **out, size_t *out_bytes,
-                            unsigned long long **mask, unsigned **first, cudaStream_t st);
+// packed: the slots hold BF16 split pairs (their value is hi + lo).
+cudaError_t compress_tensor(const float *tensor, size_t nent, int L, bool packed, double tol, float **out,
+                            size_t *out_bytes, unsigned long long **mask, unsigned **first, cudaStream_t st);
 
 // Equidistant method of Eq. FFT_3D (fft3d.cu): the z-convolution that
 // replaces the layer contraction (contract_mode 5), and the z-transform of the
@@ -181,6 +183,7 @@ struct demag_plan {
     int split = 0;                // 1: split path
     int contract_mode = 0;        // split path contraction (see ApplyArgs)
     int umajor = 0;               // blocked tensor layout [Kx][Qy][6][blocks] (dense-product plans)
+    int packed = 0;               // blocked layout of BF16 split pairs, zz negated (DEMAG_PREC_SPLIT_BF16 on path 7)
     unsigned long long *d_bmask = nullptr;  // after demag_plan_compress: kept blocks per entry
     unsigned *d_bfirst = nullptr;           // and each entry's first block
     double compress_tol = -1.0;             // < 0: not compressed

@@ -17,7 +17,10 @@
 //   N_ab = -1/(4 pi |tau|) int_tau int_tau' d_a d_b (1/|r - r'|),
 // is integrated by a composite Gauss-Legendre rule over the trapezoidal
 // density of each coordinate difference (a reading not in the paper).
+#include <cuda_bf16.h>
+
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "fft.cuh"
@@ -1035,6 +1038,18 @@ cudaError_t launch_fft2_planes(void *planes, bool f32, int nplanes, int log2Px, 
                              (const double2 *)twy, log2twy, st);
 }
 
+// The BF16 split pair of a tensor value, as the bits of a float: v rounded to
+// float, hi = bf16(v) in the upper half, lo = bf16(v - hi) in the lower half,
+// both rounded to nearest even (the split the contraction applies to its
+// other operand).
+__device__ __forceinline__ float bf16_pair(double x) {
+    const float v = (float)x;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const uint32_t w = ((uint32_t)__bfloat16_as_ushort(hi) << 16) | (uint32_t)__bfloat16_as_ushort(lo);
+    return __uint_as_float(w);
+}
+
 // Quadrant kx <= Px/2, ky <= Py/2 of the transformed planes -> plan tensor,
 // stored entry u holding ky = u_kyq(u) (layout.cuh).
 // plane 0 = FFT(N_xx) + i FFT(N_yy), both real; plane 1 = FFT(N_zz) + i FFT(N_xy),
@@ -1042,7 +1057,8 @@ cudaError_t launch_fft2_planes(void *planes, bool f32, int nplanes, int log2Px, 
 // FFT(N_yz) = i b.  Dense-product plans (umajor) write the blocked, prescaled
 // layout of layout.cuh: pair (i, j) of the pair lists, times t_i / t_0, and in
 // a diagonal block also its mirror (j, i) with xz and yz negated; the tensor
-// is zeroed beforehand (padding layers).
+// is zeroed beforehand (padding layers).  umajor 2: the same with zz negated
+// and each value as its BF16 split pair (bf16_pair).
 template <typename T, typename C>
 __global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npairs,
                           int log2Px, int log2Py, int QyS, T *__restrict__ tensor, int umajor,
@@ -1065,14 +1081,20 @@ __global__ void k_extract(const C *__restrict__ planes, int p0, int np, int npai
     if (umajor) {
         const int i = pair_i[p0 + P], j = pair_j[p0 + P], nb = ub_nb(L), rl = ub_row(L);
         const double f = sc * th[i] / th[0];
-        const double v[6] = {A.x * f, A.y * f, Bp.x * f, Bp.y * f, Cc.y * f, -Cc.x * f};
+        // umajor 2 (BF16 split plans): zz negated (the -K_zz block of the
+        // contraction) and every value stored as its BF16 split pair
+        const double zs = umajor == 2 ? -1.0 : 1.0;
+        const double v[6] = {A.x * f, A.y * f, zs * Bp.x * f, Bp.y * f, Cc.y * f, -Cc.x * f};
         T *o = tensor + ((size_t)kx * Qy + u) * (6 * (size_t)rl);
         const int I = i >> 3, J = j >> 3;
         const int e1 = ub_blk(I, J, nb) + ub_at(i & 7, j & 7, J);
-        for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e1] = (T)v[c];
+        for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e1] = umajor == 2 ? (T)bf16_pair(v[c]) : (T)v[c];
         if (I == J && i != j) {
             const int e2 = ub_blk(I, I, nb) + ub_at(j & 7, i & 7, I);
-            for (int c = 0; c < 6; ++c) o[(size_t)c * rl + e2] = (T)(c >= 4 ? -v[c] : v[c]);
+            for (int c = 0; c < 6; ++c) {
+                const double w = c >= 4 ? -v[c] : v[c];
+                o[(size_t)c * rl + e2] = umajor == 2 ? (T)bf16_pair(w) : (T)w;
+            }
         }
         return;
     }

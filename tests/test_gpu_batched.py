@@ -137,6 +137,42 @@ def test_split_bf16_plan_defaults_to_the_bf16_tcgen05_path():
         assert rel_l2(H.double().cpu().numpy(), ref) < 1e-5
 
 
+def test_bf16_plan_equals_tf32_plan_on_path_7_bit_for_bit():
+    """Path 7 splits every tensor value into BF16 hi + lo: a DEMAG_PREC_SPLIT_TF32
+    plan in the kernel, from its float tensor, a DEMAG_PREC_SPLIT_BF16 plan at
+    plan time, storing the pairs with N_zz negated.  The operands and so the
+    fields are the same, bit for bit.  Compressed, the two plans judge a block
+    by its float value and by hi + lo (within 2^-18 of it), which may part at
+    the tolerance's edge: the fields agree to 1e-6.  The BF16 plan runs path 7
+    only."""
+    nx, ny, B = 40, 36, 3
+    th = tuple(np.round(np.linspace(0.6, 2.4, 12), 3))
+    m = torch.tensor(inputs.random_unit_vectors((B, len(th), ny, nx), seed=23), dtype=torch.float32, device="cuda")
+    p32 = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=B)
+    p16 = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_BF16, max_batch=B)
+    try:
+        dm.demag_plan_set_path(p32.handle, 7)
+        assert p16.info["path"] == 7
+        for path in (3, 4, 6):
+            with pytest.raises(dm.DemagError):
+                dm.demag_plan_set_path(p16.handle, path)
+        assert torch.equal(p32.apply(m, 8e5), p16.apply(m, 8e5))
+        g32 = torch.empty_like(m)
+        g16 = torch.empty_like(m)
+        dm.demag_apply_adjoint(p32.handle, m, 3.0, g32, info=p32.info)
+        dm.demag_apply_adjoint(p16.handle, m, 3.0, g16, info=p16.info)
+        assert torch.equal(g32, g16)
+        p32.compress(1e-8)
+        p16.compress(1e-8)
+        h32, h16 = p32.apply(m, 8e5), p16.apply(m, 8e5)
+        assert float(torch.linalg.vector_norm(h32 - h16) / torch.linalg.vector_norm(h32)) < 1e-6
+        torch.cuda.synchronize()
+        assert dm.demag_wait_timeouts() == 0
+    finally:
+        p32.close()
+        p16.close()
+
+
 @pytest.mark.parametrize("prec,nx,ny,th,shrinks", [
     (dm.PREC_SPLIT_BF16, 64, 48, tuple(np.round(np.linspace(0.6, 2.4, 20), 3)), False),
     (dm.PREC_SPLIT_TF32, 40, 36, tuple(np.round(np.linspace(0.5, 3.0, 24), 3)), False),

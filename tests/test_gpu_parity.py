@@ -315,17 +315,22 @@ def test_gpu_argument_errors():
     plan.close()
 
 
-@pytest.mark.parametrize("nx,ny,th", [(7, 5, (1.0, 0.5, 2.0)),
-                                      (9, 6, tuple(np.round(np.linspace(0.6, 2.4, 10), 3)))])
-def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
+@pytest.mark.parametrize("nx,ny,th,prec", [(7, 5, (1.0, 0.5, 2.0), dm.PREC_SPLIT_TF32),
+                                           (9, 6, tuple(np.round(np.linspace(0.6, 2.4, 10), 3)), dm.PREC_SPLIT_TF32),
+                                           (9, 6, tuple(np.round(np.linspace(0.6, 2.4, 10), 3)), dm.PREC_SPLIT_BF16)])
+def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th, prec):
     """A dense-product plan's stored tensor, decoded here from the documented
     blocked layout (8 x 8 layer blocks R <= C of M(i, j) = (t_i / t_0) N(i <- j),
     half h = b / 4 of row a of block (R, C) in 16-byte slot a ^ (C mod 4) ^ 4 h
     of half-block h, diagonal blocks mirrored
     with xz and yz negated, layers past L zero), equals
-    the oracle's transformed kernels.  10 layers cross a block boundary."""
-    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=dm.PREC_SPLIT_TF32, max_batch=1)
+    the oracle's transformed kernels.  10 layers cross a block boundary.  A
+    DEMAG_PREC_SPLIT_BF16 plan on path 7 stores each value as its BF16 split
+    pair (hi << 16 | lo, hi + lo within 2^-18 of the value) and N_zz negated."""
+    plan = dm.Plan(nx, ny, 2.0, 2.0, th, precision=prec, max_batch=1)
     info = plan.info
+    packed = prec == dm.PREC_SPLIT_BF16
+    assert info["path"] == 7 or not packed
     Px, Py, L = info["Px"], info["Py"], info["L"]
     Kx, Qy = Px // 2 + 1, Py // 2 + 1
     nb = (L + 7) // 8
@@ -333,7 +338,13 @@ def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
     out = torch.empty(Kx * Qy * 6 * row, dtype=torch.float32, device="cuda")
     dm.demag_plan_tensor(plan.handle, out)
     torch.cuda.synchronize()
-    T = out.cpu().numpy().astype(np.float64).reshape(Kx, Qy, 6, row)
+    if packed:
+        w = out.cpu().numpy().view(np.uint32)
+        hi = (w & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
+        lo = (w << np.uint32(16)).view(np.float32).astype(np.float64)
+        T = (hi + lo).reshape(Kx, Qy, 6, row)
+    else:
+        T = out.cpu().numpy().astype(np.float64).reshape(Kx, Qy, 6, row)
     plan.close()
     ky_of_u = _stored_ky(Py, info["path"])
     K = reading_kernels(nx, ny, 2.0, 2.0, tuple(th))
@@ -348,6 +359,7 @@ def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
             R = np.stack([S[0].real, S[1].real, S[2].real, S[3].real, S[4].imag, S[5].imag])
             ref[i, j] = np.transpose(R[:, ky_of_u, :Kx], (2, 1, 0))  # [kx, u, component]
     sign = np.array([1.0, 1.0, 1.0, 1.0, -1.0, -1.0])
+    zz = np.array([1.0, 1.0, -1.0 if packed else 1.0, 1.0, 1.0, 1.0])
     exp = np.zeros_like(T)
     blk = 0
     for Rb in range(nb):
@@ -360,9 +372,9 @@ def test_split_plan_tensor_matches_oracle_in_the_blocked_layout(nx, ny, th):
                     h = b // 4  # half-row h of row a in slot a ^ (Cb mod 4) ^ 4h of half-block h
                     e = 64 * blk + 32 * h + 4 * (a ^ (Cb & 3) ^ (4 * h)) + (b & 3)
                     if i <= j:
-                        exp[:, :, :, e] = th[i] / th[0] * ref[i, j]
+                        exp[:, :, :, e] = zz * th[i] / th[0] * ref[i, j]
                     else:  # lower half of a diagonal block
-                        exp[:, :, :, e] = sign * th[j] / th[0] * ref[j, i]
+                        exp[:, :, :, e] = zz * sign * th[j] / th[0] * ref[j, i]
             blk += 1
     sc = np.abs(exp).max()
-    assert np.abs(T - exp).max() < 2e-6 * sc
+    assert np.abs(T - exp).max() < (5e-6 if packed else 2e-6) * sc
