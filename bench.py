@@ -502,14 +502,32 @@ def mram_block(args, world, rank, dist, peaks, with_oracle):
         flush.fill_(float(k))
         stage += np.array(dm.demag_apply_timed(plan.handle, m, Ms, H, stream, info)[:3])
     stage /= nk
-    mh = torch.tensor(m_np, dtype=torch.float32).pin_memory()
-    Hh = torch.empty_like(mh).pin_memory()
-    dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
+    # end to end on page-locked host buffers, every evaluation copying its state
+    # in and its field out.  Streamed (the value): demag_apply_host_async on two
+    # alternating buffer sets, one evaluation's copies overlapping another's
+    # kernels; one call at a time: demag_apply_host (the kernels read m and
+    # write H over the host link), synchronised every call
+    H_dev = H.clone().cpu()
+    mh = [torch.tensor(m_np, dtype=torch.float32).pin_memory() for _ in range(2)]
+    Hh = [torch.empty_like(mh[0]).pin_memory() for _ in range(2)]
     ne = min(steps, 200)
+    for k in range(2):
+        dm.demag_apply_host_async(plan.handle, mh[k], Ms, Hh[k], stream, info)
+    dm.demag_apply_host_wait(plan.handle, stream)
+    if dist:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for k in range(ne):
+        dm.demag_apply_host_async(plan.handle, mh[k & 1], Ms, Hh[k & 1], stream, info)
+    dm.demag_apply_host_wait(plan.handle, stream)
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
+    e2e_match = bool(torch.equal(Hh[0], H_dev) and torch.equal(Hh[1], H_dev))
+    dm.demag_apply_host(plan.handle, mh[0], Ms, Hh[0], stream, info)
     e0 = time.perf_counter()
     for _ in range(ne):
-        dm.demag_apply_host(plan.handle, mh, Ms, Hh, stream, info)
-    e2e_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
+        dm.demag_apply_host(plan.handle, mh[0], Ms, Hh[0], stream, info)
+    sync_s = max_over_ranks((time.perf_counter() - e0) / ne, dist, "cuda")
+    e2e_match = e2e_match and bool(torch.equal(Hh[0], H_dev))
     Kx, Qy, npairs = info["Px"] // 2 + 1, info["Py"] // 2 + 1, info["npairs"]
     field = B * L * 3 * ny * nx * 4
     spec = B * L * 3 * Kx * ny * 8
@@ -533,7 +551,15 @@ def mram_block(args, world, rank, dist, peaks, with_oracle):
                         "frac": achieved / peak, "traffic": recorded_traffic(names[dom]),
                         "algorithmic_bytes": stage_bytes[dom]},
            "e2e": {"value": whole_job_value(world, B, e2e_s * 1e3), "unit": "evals/s",
-                   "h2d_bytes_per_step": field, "d2h_bytes_per_step": field},
+                   "h2d_bytes_per_step": field, "d2h_bytes_per_step": field,
+                   "how": "demag_apply_host_async on page-locked buffers, %d consecutive evaluations (each "
+                          "copies its state in and its field out, overlapping another's kernels), then "
+                          "demag_apply_host_wait; no L2 flush between evaluations (the 57 MB tensor stays in "
+                          "L2, as in a loop of evaluations), unlike the device timing's cold L2 per step" % ne,
+                   "one_call_at_a_time": {"value": whole_job_value(world, B, sync_s * 1e3), "unit": "evals/s",
+                                          "how": "demag_apply_host on device-mapped page-locked buffers, "
+                                                 "synchronised every call (%d calls)" % ne},
+                   "field_equals_device_run": e2e_match},
            "plan_create_s": plan_s, "rel_l2_vs_oracle": None, "cpu_baseline": None}
     if rank == 0 and with_oracle:
         Khat = oracle_setup(c, th)
