@@ -20,6 +20,20 @@ namespace {
 
 using namespace f1024;
 
+// Item e of the forward transform's untangling phase (ny even) -> x-frequency
+// kx; its row pair is e mod 8.  Each 8 lanes take the 8 row pairs of one kx (one 128-byte run of
+// the spectrum), and a half-warp's two kx are two apart (kx, kx + 2 of a group
+// of four), so that their padded column slots differ by one and the 16 lanes'
+// shared-memory accesses (plane stride 1150, even) meet 16 bank pairs instead
+// of 8.  Items 4096..4103 give kx = 512.  (The inverse transform's placing
+// stores have the same 2-way pattern; the same mapping there measured slower,
+// 2.20 -> 2.24 ms at 512 x 512 x 64 x 16, and is not used.)
+static_assert(kF10Planes == 8, "r10_kx maps 8 row pairs per kx");
+__device__ __forceinline__ int r10_kx(int e) {
+    const int s = (e >> 3) & 3;
+    return 4 * (e >> 5) + (((s & 1) << 1) | (s >> 1));
+}
+
 constexpr int kR10Rows = 2 * kF10Planes;  // rows per block
 
 __global__ void __launch_bounds__(kF10Threads, 2) k_rows_forward1024(const float *__restrict__ m,
@@ -63,7 +77,7 @@ __global__ void __launch_bounds__(kF10Threads, 2) k_rows_forward1024(const float
         // and b of the pair are adjacent in the spectrum, so both leave in one
         // 16-byte store (ny even) from one pair of reads
         for (int e = threadIdx.x; e < 513 * kF10Planes; e += kF10Threads) {
-            const int kx = e / kF10Planes, q = e % kF10Planes;
+            const int kx = r10_kx(e), q = e % kF10Planes;
             const int ya = y0 + 2 * q;
             if (ya >= ny) continue;
             const float2 *zp = buf + q * kF10Plane;
