@@ -21,6 +21,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 from paper_1910_07054_gb300.sharded import ShardedApply, even_ranges  # noqa: E402
 
 STEPS = r"""
+import os
 import numpy as np
 import torch
 from oracle import demag as odm
@@ -68,7 +69,8 @@ def run(rank, world, dist):
     def rows_inverse(spec, p0, p1):
         H[p0:p1] = -Ms * torch.fft.irfft(spec.transpose(1, 2), n=2 * nx, dim=2)[:, :, :nx]
 
-    sa = ShardedApply(P, Kx, ny, rank, world, rows_forward, columns_slab, rows_inverse, dist)
+    stage = os.environ.get("DEMAG_STAGE_HOST") == "1"
+    sa = ShardedApply(P, Kx, ny, rank, world, rows_forward, columns_slab, rows_inverse, dist, stage_host=stage)
     sa.apply()
     p0, p1 = sa.planes[rank]
     return H[p0:p1].numpy(), (p0, p1), sa
@@ -130,13 +132,16 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def test_two_gloo_ranks_equal_one_rank_bit_for_bit(tmp_path):
+@pytest.mark.parametrize("stage_host", ["0", "1"])
+def test_two_gloo_ranks_equal_one_rank_bit_for_bit(tmp_path, stage_host):
+    """Both exchange modes: in place, and staged through host memory (the mode
+    of gloo ranks whose spectra live on a GPU; here a copy of a host tensor)."""
     port = _free_port()
     out = str(tmp_path / "H.npy")
     procs = []
     for rank in range(2):
         env = dict(os.environ, WORLD_SIZE="2", RANK=str(rank), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
-                   DEMAG_ROOT=ROOT, DEMAG_STEPS=STEPS, DEMAG_OUT=out)
+                   DEMAG_ROOT=ROOT, DEMAG_STEPS=STEPS, DEMAG_OUT=out, DEMAG_STAGE_HOST=stage_host)
         procs.append(subprocess.Popen([sys.executable, "-c", RANK_SCRIPT], env=env, stdout=subprocess.PIPE,
                                       stderr=subprocess.PIPE, text=True, cwd=ROOT))
     infos = []
