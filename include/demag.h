@@ -416,7 +416,8 @@ demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_b
 
 /*
  * demag_plan_keep_slab - keep only the x-frequencies k0 <= kx < k1 of the
- * plan's tensor (and shrink its column workspace to them), freeing the rest.
+ * plan's tensor, freeing the rest, and shrink its column workspace to them
+ * (where the smaller workspace can be allocated; else the full one stays).
  *
  *   plan     a hybrid plan on the split path (DEMAG_PREC_SPLIT_TF32 or
  *            DEMAG_PREC_SPLIT_BF16 plans, or another plan after
@@ -428,7 +429,7 @@ demag_status demag_plan_compress(demag_plan_t plan, double tol, size_t *stored_b
  * built on it return DEMAG_EUNSUPPORTED, and demag_plan_tensor copies out the
  * slab.  Errors: DEMAG_EINVAL (NULL plan, range), DEMAG_EUNSUPPORTED (another
  * path or method, a compressed tensor, already a slab), DEMAG_ENOMEM /
- * DEMAG_ECUDA.
+ * DEMAG_ECUDA (the slab's copy could not be made: the plan is unchanged).
  */
 demag_status demag_plan_keep_slab(demag_plan_t plan, int k0, int k1);
 

@@ -925,15 +925,18 @@ demag_status demag_plan_keep_slab(demag_plan_t plan, int k0, int k1) {
     plan->slab_k0 = k0;
     plan->slab_k1 = k1;
     // the row spectrum workspace serves demag_apply only; the column
-    // workspace shrinks to the slab
+    // workspace shrinks to the slab where a smaller one can be had (else the
+    // plan keeps the full one, which holds any slab)
     cudaFree(plan->d_spec);
     plan->d_spec = nullptr;
     const bool fp64 = plan->precision == DEMAG_PREC_FP64;
     const size_t w2 = split_workspace_bytes(plan->L, plan->max_batch, plan->log2Px, plan->log2Py, fp64) /
                       plan->Kx * (k1 - k0);
-    cudaFree(plan->d_spec2);
-    plan->d_spec2 = nullptr;
-    DEMAG_TRY(dalloc(&plan->d_spec2, w2, "column workspace"));
+    void *ws = nullptr;
+    if (dalloc(&ws, w2, "column workspace of the slab") == DEMAG_OK) {
+        cudaFree(plan->d_spec2);
+        plan->d_spec2 = ws;
+    }
     return DEMAG_OK;
 }
 
