@@ -609,7 +609,9 @@ def batched_measurement(steps, peaks, n=512, layers=64, paths=(6, 7, 4, 3)):
             use = plan
             dm.demag_plan_set_path(use.handle, path)
         info = dm.demag_plan_info(use.handle)
-        assert info["path"] == path
+        if info["path"] != path:  # e.g. odd L: the tcgen05 kernel does not hold the plan
+            out[name] = {"skipped": "the plan runs path %d, not %d" % (info["path"], path)}
+            continue
         dm.demag_apply(use.handle, m, inputs.MS_DEFAULT, H, info=info)
         st = np.mean([dm.demag_apply_timed(use.handle, m, inputs.MS_DEFAULT, H, info=info)
                       for _ in range(steps)], axis=0)
@@ -623,7 +625,7 @@ def batched_measurement(steps, peaks, n=512, layers=64, paths=(6, 7, 4, 3)):
                      "contraction_tflops_useful": flops / (st[4] * 1e-3) / 1e12}
     bf16_peak = float(peaks.get("bf16_tflops", 1894.6))
     for name in ("tensor_cores_3xtf32", "tcgen05_3xtf32", "tcgen05_3xbf16"):
-        if name not in out:
+        if name not in out or "skipped" in out[name]:
             continue
         tc = out[name]
         bf = name == "tcgen05_3xbf16"
