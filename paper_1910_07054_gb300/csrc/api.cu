@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "nvtx.cuh"
 #include "mbar.cuh"
 #include "layout.cuh"
 
@@ -365,6 +366,7 @@ demag_status demag_wait_timeouts(unsigned long long *count) {
 static demag_status plan_create_impl(demag_plan_t *plan, int nx, int ny, double dx, double dy,
                                      const double *thickness, int L, int precision, int max_batch,
                                      void *stream, int method) {
+    NvtxRange nvtx_range("demag plan build");
     g_last_error.clear();
     if (!plan) return fail(DEMAG_EINVAL, "plan pointer is NULL");
     if (!thickness) return fail(DEMAG_EINVAL, "thickness pointer is NULL");

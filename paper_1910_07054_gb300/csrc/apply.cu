@@ -24,6 +24,7 @@
 #include "fft.cuh"
 #include "internal.h"
 #include "layout.cuh"
+#include "nvtx.cuh"
 
 namespace demag {
 
@@ -365,16 +366,26 @@ static cudaError_t apply_impl(const ApplyArgs &a, const T *m, T *H, cudaStream_t
                               cudaEvent_t *ev) {
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-    if ((e = rows_stage<T>(a, m, H, true, st)) != cudaSuccess) return e;
+    {
+        NvtxRange r("demag rows forward");
+        if ((e = rows_stage<T>(a, m, H, true, st)) != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-    if ((e = columns_stage<T>(a, st)) != cudaSuccess) return e;
+    {
+        NvtxRange r("demag columns and layer sum");
+        if ((e = columns_stage<T>(a, st)) != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-    if ((e = rows_stage<T>(a, m, H, false, st)) != cudaSuccess) return e;
+    {
+        NvtxRange r("demag rows inverse");
+        if ((e = rows_stage<T>(a, m, H, false, st)) != cudaSuccess) return e;
+    }
     if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
 cudaError_t launch_apply_stage(const ApplyArgs &a, int stage, const void *m, void *H, bool fp64, cudaStream_t st) {
+    NvtxRange r(stage == 0 ? "demag rows forward" : stage == 1 ? "demag columns and layer sum" : "demag rows inverse");
     if (stage == 1) return fp64 ? columns_stage<double>(a, st) : columns_stage<float>(a, st);
     if (fp64) return rows_stage<double>(a, (const double *)m, (double *)H, stage == 0, st);
     return rows_stage<float>(a, (const float *)m, (float *)H, stage == 0, st);

@@ -62,17 +62,25 @@ def generate_samples(solver, thicknesses):
     return np.asarray(thicknesses, dtype=np.float64), Y
 
 
+def save_samples(path, T, Y):
+    """Cache a training set (one exact solve per row) in an .npz file."""
+    np.savez(path, T=np.asarray(T, dtype=np.float64), Y=np.asarray(Y, dtype=np.float64))
+
+
+def load_samples(path):
+    """(T, Y) from save_samples."""
+    with np.load(path) as f:
+        return f["T"].copy(), f["Y"].copy()
+
+
 class Surrogate:
     """I -> H -> H -> H -> O tanh network in bf16 weights / float sums."""
 
-    def __init__(self, I=8, H=64, O=3, seed=0):
+    def __init__(self, I=8, H=64, O=3, seed=0, device="cuda"):
         self.I, self.H, self.O = I, H, O
+        self.device = device
         self.P = _lib.demag_mlp_param_count(I, H, O)
-        w0 = inputs.mlp_init(I, H, O, seed)
-        self.w = torch.tensor(w0, device="cuda")
-        _, bits = inputs.bf16_round(w0)
-        self.wb = torch.from_numpy(bits.view(np.int16)).to("cuda").view(torch.bfloat16)
-        self.g = torch.zeros_like(self.w)
+        self._set_weights(inputs.mlp_init(I, H, O, seed))
         self.m1 = torch.zeros_like(self.w)
         self.m2 = torch.zeros_like(self.w)
         self.step = 0
@@ -80,9 +88,46 @@ class Surrogate:
         self.x_std = np.ones(I)
         self.y_scale = np.ones(O)
 
+    def _set_weights(self, w0):
+        # float master weights, their bf16 copy (what the kernels read) and the gradient
+        w0 = np.asarray(w0, dtype=np.float32)
+        self.w = torch.tensor(w0, device=self.device)
+        _, bits = inputs.bf16_round(w0)
+        self.wb = torch.from_numpy(bits.view(np.int16)).to(self.device).view(torch.bfloat16)
+        self.g = torch.zeros_like(self.w)
+
+    def state(self):
+        """Everything training needs to resume: master weights, Adam moments and
+        step, and the input / output normalisation (numpy arrays)."""
+        return {"shape": np.array([self.I, self.H, self.O]), "w": self.w.cpu().numpy(),
+                "m1": self.m1.cpu().numpy(), "m2": self.m2.cpu().numpy(), "step": np.array(self.step),
+                "x_mean": np.asarray(self.x_mean), "x_std": np.asarray(self.x_std),
+                "y_scale": np.asarray(self.y_scale)}
+
+    def save(self, path):
+        """Checkpoint the network (state()) to an .npz file."""
+        np.savez(path, **self.state())
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        """A network restored from save(): fit() continues its Adam run."""
+        with np.load(path) as f:
+            st = {k: f[k].copy() for k in f.files}
+        I, H, O = (int(v) for v in st["shape"])
+        net = cls(I, H, O, device=device)
+        if st["w"].shape != (net.P,):
+            raise ValueError("checkpoint holds %d parameters, an %d-%d-%d network has %d"
+                             % (st["w"].size, I, H, O, net.P))
+        net._set_weights(st["w"])
+        net.m1 = torch.tensor(st["m1"], device=device)
+        net.m2 = torch.tensor(st["m2"], device=device)
+        net.step = int(st["step"])
+        net.x_mean, net.x_std, net.y_scale = st["x_mean"], st["x_std"], st["y_scale"]
+        return net
+
     def _x(self, t):
         x = (np.atleast_2d(t) - self.x_mean) / self.x_std
-        return torch.tensor(x, dtype=torch.float32, device="cuda").contiguous()
+        return torch.tensor(x, dtype=torch.float32, device=self.device).contiguous()
 
     def fit(self, T, Y, steps=3000, lr=3e-3, log_every=0):
         """Full-batch Adam on the mean squared error of the scaled outputs."""
@@ -90,10 +135,10 @@ class Surrogate:
         self.x_mean, self.x_std = T.mean(0), T.std(0) + 1e-12
         self.y_scale = np.abs(Y).max(0) + 1e-30
         x = self._x(T)
-        yt = torch.tensor(Y / self.y_scale, dtype=torch.float32, device="cuda").contiguous()
+        yt = torch.tensor(Y / self.y_scale, dtype=torch.float32, device=self.device).contiguous()
         y = torch.empty_like(yt)
         gy = torch.empty_like(yt)
-        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
         history = []
         for k in range(steps):
             loss.zero_()
@@ -110,14 +155,14 @@ class Surrogate:
 
     def predict(self, t):
         x = self._x(t)
-        y = torch.empty(x.shape[0], self.O, dtype=torch.float32, device="cuda")
+        y = torch.empty(x.shape[0], self.O, dtype=torch.float32, device=self.device)
         _lib.demag_mlp_forward(self.wb, x, y, self.I, self.H, self.O)
         return y.double().cpu().numpy() * self.y_scale
 
     def slope(self, t, out=2, layer=inputs.OPT_LAYER):
         """d(output `out`)/d t[layer] through the network (its input gradient)."""
         x = self._x(t)
-        gy = torch.zeros(x.shape[0], self.O, dtype=torch.float32, device="cuda")
+        gy = torch.zeros(x.shape[0], self.O, dtype=torch.float32, device=self.device)
         gy[:, out] = 1.0
         gx = torch.empty_like(x)
         _lib.demag_mlp_backward(self.wb, x, gy, None, gx, self.I, self.H, self.O)
